@@ -1,0 +1,229 @@
+/*
+ * mdwf.h -- C ABI of libmdwf: the even-odd preconditioned Moebius domain-wall fermion
+ * (MDWF) propagator solve of arXiv:1810.01609 on one NVIDIA GB300 (sm_103a).
+ *
+ * The paper (Sec. "Current State of the Art") states the problem this library solves:
+ * linear solves of the domain-wall Dirac matrix on an L^3 x T x L5 x Nc x Ns space,
+ * a radius-one stencil with small dense 12x12 diagonal blocks, by conjugate gradient
+ * on the normal equations with red-black preconditioning, in "double-half" mixed
+ * precision with reliable updates to double; the propagators feed Feynman-Hellmann
+ * sequential solves and nucleon contractions (Sec. "Performance Measurement Method").
+ *
+ * Operator conventions (the paper prints none; these are the library's readings):
+ *   chiral basis: gamma_k = [[0, i sigma_k], [-i sigma_k, 0]], gamma_4 = [[0,1],[1,0]],
+ *   gamma_5 = diag(-1,-1,1,1), P_-/P_+ = upper/lower spin pair.
+ *   H psi(x)  = sum_mu (1-gamma_mu) U_mu(x) psi(x+mu) + (1+gamma_mu) U_mu(x-mu)^+ psi(x-mu)
+ *   D_W       = (4 - M5) - H/2,  (B psi)_s = P_- psi_{s+1} + P_+ psi_{s-1},
+ *               psi_{Ls} -> -mf psi_0, psi_{-1} -> -mf psi_{Ls-1}
+ *   D         = D_W (b5 + c5 B) + (1 - B)                 (Moebius 5D operator)
+ *   D5 = b5 + c5 B,  A5 ("M5") = (4-M5) D5 + 1 - B
+ *   M_pc      = 1 - (1/4) A5^-1 H_oe D5 A5^-1 H_eo D5        (odd sites; parity x+y+z+t)
+ *
+ * Layouts
+ *   links   (user)  complex128 U[t][z][y][x][mu][a][b], mu = x,y,z,t; U_mu(x) lives on
+ *                   the link x -> x+mu.  The time boundary phase t_bc is applied by the
+ *                   library (do not fold it in).
+ *   5D field (user) complex128 psi[rhs][s][t][z][y][x][spin][colour].
+ *   4D field (user) complex128 psi[rhs][t][z][y][x][spin][colour].
+ *   4D propagator   complex128 S[12][t][z][y][x][spin][colour]: column src_spin*3 +
+ *                   src_colour holds the sink field of that source component (what
+ *                   mdwf_project_4d writes for nrhs = 12 point sources).
+ *   internal field  opaque device buffer of mdwf_field_bytes() bytes holding both
+ *                   parities in the library's Ls-inner, site-blocked, 16-byte-chunk
+ *                   layout for one precision and a given number of right-hand sides.
+ *
+ * Ownership: the caller owns every buffer passed in; the library never frees caller
+ * memory.  The context owns its internal gauge copies, workspaces and tune cache.
+ * Pointers flagged DEVICE must be device memory of the current CUDA device; pointers
+ * flagged HOST are host memory (pinned is faster).  `stream` is a cudaStream_t (NULL =
+ * legacy default stream).  All calls are stream-ordered; mdwf_solve* synchronise the
+ * stream before returning so that `info` is valid.
+ *
+ * Errors: every int-returning call returns MDWF_SUCCESS (0) or a negative MDWF_ERR_*;
+ * mdwf_strerror() names it.  Invalid arguments are rejected before any launch.
+ */
+#ifndef MDWF_H
+#define MDWF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum mdwf_status {
+  MDWF_SUCCESS = 0,
+  MDWF_ERR_ARG = -1,           /* invalid argument (null pointer, bad dims, Ls, op ...) */
+  MDWF_ERR_CUDA = -2,          /* a CUDA runtime call or kernel launch failed */
+  MDWF_ERR_OOM = -3,           /* device allocation failed */
+  MDWF_ERR_NOT_SU3 = -4,       /* mdwf_load_gauge: a link is not special unitary */
+  MDWF_ERR_NOT_CONVERGED = -5, /* maxiter reached; solution and info still written */
+  MDWF_ERR_BREAKDOWN = -6,     /* CG breakdown: NaN/Inf or non-positive p^+ A p */
+  MDWF_ERR_TIMEOUT = -7,       /* a bounded device-side wait gave up */
+  MDWF_ERR_STATE = -8          /* call out of order (e.g. no gauge field loaded) */
+};
+
+enum mdwf_precision {
+  MDWF_PREC_F64 = 0,   /* double storage, double arithmetic */
+  MDWF_PREC_F32 = 1,   /* float storage, float arithmetic */
+  MDWF_PREC_F16 = 2,   /* half storage + one float norm per 5D site, float arithmetic */
+  MDWF_PREC_BF16 = 3   /* bfloat16 storage, float arithmetic */
+};
+
+enum mdwf_location { MDWF_HOST = 0, MDWF_DEVICE = 1 };
+
+/* Operators of mdwf_apply.  "e"/"o" = even/odd half of the internal field; an op
+ * writes only the half(s) it names and leaves the rest of `out` untouched. */
+enum mdwf_op {
+  MDWF_OP_HOP_EO = 0,      /* out_e = H_eo in_o                                   */
+  MDWF_OP_HOP_OE = 1,      /* out_o = H_oe in_e                                   */
+  MDWF_OP_HOP_EO_DAG = 2,  /* out_e = H_eo^+ in_o  (H^+ = gamma5 H gamma5)        */
+  MDWF_OP_HOP_OE_DAG = 3,  /* out_o = H_oe^+ in_e                                 */
+  MDWF_OP_D5 = 4,          /* out = (b5 + c5 B) in, both parities                 */
+  MDWF_OP_D5_DAG = 5,
+  MDWF_OP_M5 = 6,          /* out = A5 in, both parities                          */
+  MDWF_OP_M5_DAG = 7,
+  MDWF_OP_M5INV = 8,       /* out = A5^-1 in, both parities                       */
+  MDWF_OP_M5INV_DAG = 9,
+  MDWF_OP_HOP_EO_M5INV = 10, /* out_e = A5^-1 H_eo in_o : the fused hop + M5^-1 kernel */
+  MDWF_OP_HOP_OE_M5INV = 11, /* out_o = A5^-1 H_oe in_e                            */
+  MDWF_OP_MPC = 12,        /* out_o = M_pc in_o                                    */
+  MDWF_OP_MPC_DAG = 13,    /* out_o = M_pc^+ in_o                                  */
+  MDWF_OP_MDAGM = 14,      /* out_o = M_pc^+ M_pc in_o                             */
+  MDWF_OP_FULL_D = 15,     /* out = D in (both parities)                           */
+  MDWF_OP_FULL_D_DAG = 16, /* out = D^+ in                                         */
+  MDWF_OP_COUNT = 17
+};
+
+typedef struct mdwf_params {
+  int dims[4];        /* X, Y, Z, T: each even and >= 2 */
+  int Ls;             /* fifth-dimension extent, 2 <= Ls <= 32 */
+  double b5, c5;      /* Moebius coefficients (b5 - c5 = 1 gives Shamir-like scaling) */
+  double M5;          /* domain-wall height */
+  double mf;          /* quark mass m_f */
+  double t_bc;        /* time boundary phase (-1 antiperiodic, +1 periodic) */
+  int gauge_recon;    /* 18: store all 18 reals of a link; 12: store two rows and
+                         rebuild the third as conj(row0 x row1) */
+  int check_su3;      /* nonzero: mdwf_load_gauge rejects links with |U U^+ - 1| or
+                         |det U - 1| above 1e-9 (MDWF_ERR_NOT_SU3) */
+} mdwf_params;
+
+typedef struct mdwf_solve_params {
+  double tol;          /* target true relative residual |b~ - M_pc x| / |b~| */
+  int maxiter;         /* inner iteration cap */
+  int sloppy_prec;     /* MDWF_PREC_F64: plain FP64 CG; F32/F16/BF16: mixed-precision CG
+                          whose inner iterations store fields in that precision and
+                          reliable-update to FP64 */
+  double delta;        /* reliable update when |r| < delta * max |r| since the last one */
+  int ru_interval;     /* ... or after this many inner iterations */
+  int check_interval;  /* iterations between host polls (and per captured CUDA graph) */
+  int use_graph;       /* nonzero: replay the check_interval iterations as a CUDA graph */
+  int location;        /* MDWF_HOST or MDWF_DEVICE for src / sol */
+  int full_residual;   /* nonzero: also compute |b - D x| / |b| (two extra FP64 hops) */
+} mdwf_solve_params;
+
+typedef struct mdwf_solve_info {
+  int status;              /* MDWF_SUCCESS or MDWF_ERR_NOT_CONVERGED / _BREAKDOWN */
+  int iterations;          /* inner CG iterations */
+  int reliable_updates;    /* FP64 residual recomputations (mixed precision) */
+  double true_residual;    /* FP64 |b~ - M_pc x| / |b~| of the preconditioned system */
+  double full_residual;    /* FP64 |b - D x| / |b| (if requested, else -1) */
+  double time_ms;          /* wall time of the call (host clock, stream synchronised) */
+} mdwf_solve_info;
+
+typedef struct mdwf_ctx mdwf_ctx;
+
+/* Fill *p with defaults: dims 4^4, Ls 8, b5 1.5, c5 0.5, M5 1.3, mf 0.05, t_bc -1,
+ * recon 18, check_su3 1. */
+void mdwf_default_params(mdwf_params* p);
+/* Defaults: tol 1e-10, maxiter 100000, sloppy F16, delta 0.1, ru_interval 100,
+ * check_interval 10, use_graph 1, location DEVICE, full_residual 1. */
+void mdwf_default_solve_params(mdwf_solve_params* sp);
+
+/* Create a context on the current CUDA device.  Validates the parameters
+ * (MDWF_ERR_ARG).  Allocates nothing on the device until a gauge field is loaded. */
+int mdwf_create(const mdwf_params* p, mdwf_ctx** out);
+/* Free every device buffer of the context and the context itself (NULL is a no-op). */
+void mdwf_destroy(mdwf_ctx* ctx);
+
+/* Load the gauge links (user layout above, complex128; `where` = MDWF_HOST/DEVICE) into
+ * the context's internal SoA layout: per parity and site, the 4 forward links U_mu(x) and
+ * the 4 backward links U_mu(x-mu)^+ with the boundary phase folded in.  The lower
+ * precision copies are made on first use.  Returns MDWF_ERR_NOT_SU3 if check_su3 is set
+ * and a link is not in SU(3). */
+int mdwf_load_gauge(mdwf_ctx* ctx, const double* links, int where, void* stream);
+
+/* Bytes of one internal field (both parities) of precision `prec` and nrhs right-hand
+ * sides. */
+int mdwf_field_bytes(const mdwf_ctx* ctx, int prec, int nrhs, size_t* bytes);
+
+/* user5d (DEVICE, complex128 [nrhs][s][t][z][y][x][4][3]) -> internal field (DEVICE).
+ * F16 stores per 5D site norm = float(max |component|) and halves = RNE(v / norm);
+ * BF16 and F32 are RNE conversions. */
+int mdwf_pack(mdwf_ctx* ctx, const double* user5d, void* internal, int prec, int nrhs,
+              void* stream);
+/* internal field (DEVICE) -> user5d (DEVICE, complex128). */
+int mdwf_unpack(mdwf_ctx* ctx, const void* internal, double* user5d, int prec, int nrhs,
+                void* stream);
+
+/* out = op(in) on internal fields (DEVICE, precision prec, nrhs right-hand sides).
+ * `in` and `out` must not overlap.  Needs a loaded gauge field (MDWF_ERR_STATE). */
+int mdwf_apply(mdwf_ctx* ctx, int op, int prec, const void* in, void* out, int nrhs,
+               void* stream);
+
+/* Solve D x = b for one 5D source: b~_o = A5^-1 (b_o + H_oe D5 A5^-1 b_e / 2), CG on
+ * M_pc^+ M_pc to |b~ - M_pc x_o| <= tol |b~| (FP64-recomputed), then
+ * x_e = A5^-1 (b_e + H_eo D5 x_o / 2).  src/sol are user 5D fields at sp->location.
+ * Returns MDWF_SUCCESS, MDWF_ERR_NOT_CONVERGED (solution still written) or an error. */
+int mdwf_solve(mdwf_ctx* ctx, const double* src, double* sol,
+               const mdwf_solve_params* sp, mdwf_solve_info* info, void* stream);
+/* The same for nrhs sources in one batched solve (contiguous [nrhs][...] user fields);
+ * link loads are shared across the right-hand sides and each has its own CG scalars.
+ * info points to nrhs entries.  The return value is the worst status. */
+int mdwf_solve_multi(mdwf_ctx* ctx, int nrhs, const double* src, double* sol,
+                     const mdwf_solve_params* sp, mdwf_solve_info* info, void* stream);
+
+/* 4D source -> 5D source: eta = D(mf=1) P (b at s=0), (P psi)_s = P_- psi_s + P_+ psi_{s+1}
+ * (Pauli-Villars injection; q below is then D_eff^-1 b).  src4d [nrhs][t][z][y][x][4][3],
+ * src5d [nrhs][s][...], both complex128 at `where`. */
+int mdwf_make_source_4d(mdwf_ctx* ctx, const double* src4d, double* src5d, int nrhs,
+                        int where, void* stream);
+/* 5D solution -> 4D propagator column q = P_- y_0 + P_+ y_{Ls-1}. */
+int mdwf_project_4d(mdwf_ctx* ctx, const double* sol5d, double* q4d, int nrhs, int where,
+                    void* stream);
+/* Feynman-Hellmann sequential source (Sec. "Current State of the Art": all temporal
+ * distances for the cost of one): out(z) = gamma_3 gamma_5 q(z) at every site z of every
+ * timeslice, for nrhs 4D columns. */
+int mdwf_fh_source(mdwf_ctx* ctx, const double* q4d, double* out4d, int nrhs, int where,
+                   void* stream);
+/* Nucleon two-point function C(t) = sum_x Tr[(1+gamma_4)/2 G(x)] of
+ * N = eps_abc (u_a^T C gamma_5 d_b) u_c, C = gamma_2 gamma_4, with both Wick terms of the
+ * two u lines (u1 = line of the sink u_a, u2 = line of the sink u_c) and the d line, in
+ * FP64.  u1, d, u2 are 4D propagators (12-column layout above); corr receives T complex values
+ * (2T doubles).  All at `where`. */
+int mdwf_contract_nucleon(mdwf_ctx* ctx, const double* u1, const double* d,
+                          const double* u2, double* corr, int where, void* stream);
+
+/* Autotuner control: enable (1) / disable (0) brute-force launch tuning (default from
+ * env MDWF_TUNE, on).  The cache is a std::map keyed by kernel, lattice, Ls, nrhs,
+ * precision and mode; MDWF_TUNE_CACHE names a JSON file it is loaded from and saved to. */
+int mdwf_set_tuning(mdwf_ctx* ctx, int enable);
+/* Number of tune-cache entries, and the tuned sites-per-CTA of entry i with its time (ms)
+ * and key (copied into key[keylen]). */
+int mdwf_tune_entries(const mdwf_ctx* ctx, int* count);
+int mdwf_tune_entry(const mdwf_ctx* ctx, int i, char* key, int keylen, int* sites_per_cta,
+                    double* ms);
+
+/* Number of kernels this context has launched so far (all streams). */
+long long mdwf_launch_count(const mdwf_ctx* ctx);
+
+/* Name of a status code. */
+const char* mdwf_strerror(int status);
+/* Detail of the last failure on the calling host thread (empty if none). */
+const char* mdwf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MDWF_H */

@@ -1,0 +1,346 @@
+// Internal definitions of libmdwf: precision traits, field and gauge layouts, lattice
+// geometry, s-direction operators and deterministic FP64 reductions.
+//
+// Internal spinor layout (one parity half of a field; Ls-inner, site-blocked):
+//   16-byte chunk (x_cb, c, r, s) at  (x_cb * NC + c) * W + (r * Ls + s),  W = nrhs * Ls
+// so that the nrhs * Ls threads of one 4D site read consecutive chunks.  A site's 24
+// reals are ordered [colour][spin][re,im]; an F16/BF16 chunk is one colour (4 spins).
+// F16 keeps one float norm per 5D site at norm[x_cb * W + r * Ls + s].
+//
+// Internal gauge layout (per parity): link (x_cb, dir) at (x_cb * 8 + dir) * GS reals,
+// dir 0..3 = U_mu(x), dir 4..7 = U_mu(x - mu)^+, boundary phase folded in (recon 18) or
+// re-applied after rebuilding the third row (recon 12).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace mdwf {
+
+enum Prec { F64 = 0, F32 = 1, F16 = 2, BF16 = 3 };
+constexpr int MAXLS = 32;
+constexpr int MAXTHREADS = 256;  // threads per CTA of site-tiled kernels (NS * nrhs * Ls)
+
+template <int P> struct PT;
+template <> struct PT<F64> {
+  using C = double; using S = double; using G = double;
+  static constexpr int NC = 12; static constexpr bool NORM = false;
+  static constexpr int GS18 = 18, GS12 = 12;
+};
+template <> struct PT<F32> {
+  using C = float; using S = float; using G = float;
+  static constexpr int NC = 6; static constexpr bool NORM = false;
+  static constexpr int GS18 = 20, GS12 = 12;
+};
+template <> struct PT<F16> {
+  using C = float; using S = __half; using G = __half;
+  static constexpr int NC = 3; static constexpr bool NORM = true;
+  static constexpr int GS18 = 24, GS12 = 16;
+};
+template <> struct PT<BF16> {
+  using C = float; using S = __nv_bfloat16; using G = __nv_bfloat16;
+  static constexpr int NC = 3; static constexpr bool NORM = false;
+  static constexpr int GS18 = 24, GS12 = 16;
+};
+
+inline int prec_nc(int p) { return p == F64 ? 12 : p == F32 ? 6 : 3; }
+inline bool prec_norm(int p) { return p == F16; }
+inline int gauge_stride(int p, int recon) {
+  if (recon == 12) return p == F64 || p == F32 ? 12 : 16;
+  return p == F64 ? 18 : p == F32 ? 20 : 24;
+}
+inline size_t prec_gsize(int p) { return p == F64 ? 8 : p == F32 ? 4 : 2; }
+
+// One parity half of an internal field.
+struct Field {
+  void* data;
+  float* norm;     // F16 only
+  int nrhs;
+  int Ls;
+  long long vh;    // 4D sites per parity
+  __host__ __device__ long long W() const { return (long long)nrhs * Ls; }
+};
+
+// ---------------------------------------------------------------- conversions
+template <typename T> __device__ __forceinline__ float to_f(T v);
+template <> __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// load the 24 reals of 5D site (x_cb, col = r*Ls+s) into v (compute type)
+template <int P>
+__device__ __forceinline__ void load_site(const Field& f, long long x_cb, int col,
+                                          typename PT<P>::C v[24]) {
+  const long long W = f.W();
+  if constexpr (P == F64) {
+    const double2* d = (const double2*)f.data;
+#pragma unroll
+    for (int c = 0; c < 12; c++) {
+      double2 q = __ldg(d + (x_cb * 12 + c) * W + col);
+      v[2 * c] = q.x; v[2 * c + 1] = q.y;
+    }
+  } else if constexpr (P == F32) {
+    const float4* d = (const float4*)f.data;
+#pragma unroll
+    for (int c = 0; c < 6; c++) {
+      float4 q = __ldg(d + (x_cb * 6 + c) * W + col);
+      v[4 * c] = q.x; v[4 * c + 1] = q.y; v[4 * c + 2] = q.z; v[4 * c + 3] = q.w;
+    }
+  } else {
+    const uint4* d = (const uint4*)f.data;
+    float nrm = 1.0f;
+    if constexpr (P == F16) nrm = __ldg(f.norm + x_cb * W + col);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      uint4 q = __ldg(d + (x_cb * 3 + c) * W + col);
+      const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        if constexpr (P == F16) {
+          float2 fv = __half22float2(*(const __half2*)&w[j]);
+          v[8 * c + 2 * j] = fv.x * nrm; v[8 * c + 2 * j + 1] = fv.y * nrm;
+        } else {
+          float2 fv = __bfloat1622float2(*(const __nv_bfloat162*)&w[j]);
+          v[8 * c + 2 * j] = fv.x; v[8 * c + 2 * j + 1] = fv.y;
+        }
+      }
+    }
+  }
+}
+
+// store 24 reals; returns nothing.  F16 computes the per-site max-abs norm.
+template <int P>
+__device__ __forceinline__ void store_site(const Field& f, long long x_cb, int col,
+                                           const typename PT<P>::C v[24]) {
+  const long long W = f.W();
+  if constexpr (P == F64) {
+    double2* d = (double2*)f.data;
+#pragma unroll
+    for (int c = 0; c < 12; c++) d[(x_cb * 12 + c) * W + col] = make_double2(v[2 * c], v[2 * c + 1]);
+  } else if constexpr (P == F32) {
+    float4* d = (float4*)f.data;
+#pragma unroll
+    for (int c = 0; c < 6; c++)
+      d[(x_cb * 6 + c) * W + col] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+  } else {
+    uint4* d = (uint4*)f.data;
+    float scale = 1.0f;
+    if constexpr (P == F16) {
+      float m = 0.0f;
+#pragma unroll
+      for (int i = 0; i < 24; i++) m = fmaxf(m, fabsf(v[i]));
+      f.norm[x_cb * W + col] = m;
+      scale = m > 0.0f ? 1.0f / m : 0.0f;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      uint32_t w[4];
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        if constexpr (P == F16) {
+          __half2 h = __floats2half2_rn(v[8 * c + 2 * j] * scale, v[8 * c + 2 * j + 1] * scale);
+          w[j] = *(uint32_t*)&h;
+        } else {
+          __nv_bfloat162 h = __floats2bfloat162_rn(v[8 * c + 2 * j], v[8 * c + 2 * j + 1]);
+          w[j] = *(uint32_t*)&h;
+        }
+      }
+      d[(x_cb * 3 + c) * W + col] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- geometry
+struct Geom {
+  int X, Y, Z, T, Xh;
+  long long vh;
+};
+
+__device__ __forceinline__ void cb_coords(const Geom& g, long long x_cb, int parity, int c[4]) {
+  int xh = (int)(x_cb % g.Xh);
+  long long rest = x_cb / g.Xh;
+  c[1] = (int)(rest % g.Y); rest /= g.Y;
+  c[2] = (int)(rest % g.Z);
+  c[3] = (int)(rest / g.Z);
+  c[0] = 2 * xh + ((parity + c[1] + c[2] + c[3]) & 1);
+}
+
+__device__ __forceinline__ long long cb_index(const Geom& g, const int c[4]) {
+  return ((((long long)c[3] * g.Z + c[2]) * g.Y + c[1]) * g.X + c[0]) >> 1;
+}
+
+__device__ __forceinline__ long long nbr_cb(const Geom& g, const int c[4], int mu, int dir) {
+  int n[4] = {c[0], c[1], c[2], c[3]};
+  const int L = mu == 0 ? g.X : mu == 1 ? g.Y : mu == 2 ? g.Z : g.T;
+  int v = n[mu] + dir;
+  n[mu] = v < 0 ? v + L : (v >= L ? v - L : v);
+  return cb_index(g, n);
+}
+
+// ---------------------------------------------------------------- s-direction operators
+// Each op acts on the Ls values of one real component of one (4D site, rhs).
+// The spin pair decides the shift direction: B moves P_- (spins 0,1) from s+1 and P_+
+// (spins 2,3) from s-1; B^+ swaps them.  "up" = takes s+1 with the wall -mf at Ls-1.
+enum SOpKind { SOP_NONE = 0, SOP_BIDIAG = 1, SOP_INV = 2 };
+struct SOp {
+  int kind;      // SOP_NONE / SOP_BIDIAG (a + b S) / SOP_INV ((a + b S)^-1)
+  int dag;       // use B^+ instead of B
+  double a, b;   // coefficients
+  double inv_a;  // 1/a
+  double c0;     // 1 / (a (1 + mf rho^Ls)), rho = -b/a
+  double w[MAXLS];  // w[k] = -mf rho^(k+1) c0, k = 0..Ls-2
+};
+
+struct SChain {
+  SOp op[2];
+};
+
+// In-place application of one op to the strided sequence y[s * st], s = 0..Ls-1.
+template <typename C>
+__device__ __forceinline__ void sop_apply(const SOp& o, bool up, C* y, int st, int Ls, C mf) {
+  if (o.kind == SOP_BIDIAG) {
+    const C a = (C)o.a, b = (C)o.b;
+    if (up) {
+      C y0 = y[0];
+      for (int s = 0; s < Ls - 1; s++) y[s * st] = a * y[s * st] + b * y[(s + 1) * st];
+      y[(Ls - 1) * st] = a * y[(Ls - 1) * st] - b * mf * y0;
+    } else {
+      C yl = y[(Ls - 1) * st];
+      for (int s = Ls - 1; s > 0; s--) y[s * st] = a * y[s * st] + b * y[(s - 1) * st];
+      y[0] = a * y[0] - b * mf * yl;
+    }
+  } else if (o.kind == SOP_INV) {
+    // (a + b S)^-1 with S^Ls = -mf: the last (up) / first (down) entry from the closed
+    // form sum, then a first-order recurrence back through the chain.
+    const C inv_a = (C)o.inv_a, b = (C)o.b;
+    if (up) {
+      C acc = (C)o.c0 * y[(Ls - 1) * st];
+      for (int j = 0; j < Ls - 1; j++) acc += (C)o.w[j] * y[j * st];
+      y[(Ls - 1) * st] = acc;
+      for (int s = Ls - 2; s >= 0; s--) {
+        acc = (y[s * st] - b * acc) * inv_a;
+        y[s * st] = acc;
+      }
+    } else {
+      C acc = (C)o.c0 * y[0];
+      for (int j = 0; j < Ls - 1; j++) acc += (C)o.w[j] * y[(Ls - 1 - j) * st];
+      y[0] = acc;
+      for (int s = 1; s < Ls; s++) {
+        acc = (y[s * st] - b * acc) * inv_a;
+        y[s * st] = acc;
+      }
+    }
+  }
+}
+
+template <typename C>
+__device__ __forceinline__ void chain_apply(const SChain& ch, int comp, C* y, int st, int Ls, C mf) {
+  // comp = real index within the site [colour][spin][re/im] -> spin = (comp >> 1) & 3
+  const bool lower = ((comp >> 1) & 3) >= 2;
+#pragma unroll
+  for (int i = 0; i < 2; i++) {
+    if (ch.op[i].kind == SOP_NONE) continue;
+    const bool up = (lower != (bool)ch.op[i].dag);  // B: P_- up; B^+: P_+ up
+    sop_apply(ch.op[i], up, y, st, Ls, mf);
+  }
+}
+
+// ---------------------------------------------------------------- reductions
+// Block partials -> last block sums them in a fixed order (deterministic) and runs a
+// scalar program.  partials[block * nrhs + r], counter reset by the last block.
+enum RedMode { RED_NONE = 0, RED_STORE = 1, RED_CG_ALPHA = 2, RED_CG_BETA = 3 };
+
+struct CGScalars {   // per right-hand side
+  double gamma;      // |r|^2 of the current iterate
+  double qq;         // |M p|^2
+  double alpha, beta;
+  double stop2;      // iterated-residual threshold (squared)
+  double maxr2;      // max |r|^2 since the last reliable update
+  int active;        // 0 once converged: alpha = beta = 0 freeze the iterate
+  int hit;           // gamma <= stop2 seen
+  int breakdown;
+  int pad;
+};
+
+struct Red {
+  int mode;
+  double* partials;
+  unsigned int* counter;
+  double* out;        // RED_STORE: out[r]
+  CGScalars* cg;      // RED_CG_*
+  int nrhs;
+};
+
+// Sum per-thread values (each belonging to rhs index r) over the block, then over the
+// grid.  vals: smem scratch of blockDim.x doubles; the block's threads are laid out as
+// (site_l, r, s) with s fastest, i.e. tid = (site_l * nrhs + r) * Ls + s.
+__device__ inline void block_grid_reduce(const Red& red, double v, double* sm, int Ls, int ns) {
+  const int tid = threadIdx.x;
+  const int nrhs = red.nrhs;
+  sm[tid] = v;
+  __syncthreads();
+  // stage 1: one thread per (site_l, r) sums its Ls values
+  const int ngrp = ns * nrhs;
+  double* sm2 = sm + blockDim.x;
+  if (tid < ngrp) {
+    double acc = 0.0;
+    for (int s = 0; s < Ls; s++) acc += sm[tid * Ls + s];
+    sm2[tid] = acc;
+  }
+  __syncthreads();
+  if (tid < nrhs) {
+    double acc = 0.0;
+    for (int i = 0; i < ns; i++) acc += sm2[i * nrhs + tid];
+    red.partials[(long long)blockIdx.x * nrhs + tid] = acc;
+  }
+  __shared__ unsigned int ticket;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) ticket = atomicAdd(red.counter, 1u);
+  __syncthreads();
+  if (ticket != gridDim.x - 1) return;
+  __threadfence();
+  // last block: fixed-order sums over blocks
+  const int nb = gridDim.x;
+  for (int r = 0; r < nrhs; r++) {
+    double acc = 0.0;
+    for (int b = tid; b < nb; b += blockDim.x) acc += __ldcg(red.partials + (long long)b * nrhs + r);
+    sm[tid] = acc;
+    __syncthreads();
+    for (int w = blockDim.x; w > 1;) {
+      int h = (w + 1) >> 1;
+      if (tid < w - h) sm[tid] += sm[tid + h];
+      __syncthreads();
+      w = h;
+    }
+    if (tid == 0) {
+      const double tot = sm[0];
+      if (red.mode == RED_STORE) {
+        red.out[r] = tot;
+      } else if (red.mode == RED_CG_ALPHA) {
+        CGScalars& c = red.cg[r];
+        c.qq = tot;
+        if (!(tot == tot) || tot <= 0.0) {
+          if (c.active && c.gamma > 0.0) c.breakdown = 1;
+          c.alpha = 0.0;
+        } else {
+          c.alpha = c.active ? c.gamma / tot : 0.0;
+        }
+      } else if (red.mode == RED_CG_BETA) {
+        CGScalars& c = red.cg[r];
+        if (c.active) {
+          if (!(tot == tot)) c.breakdown = 1;
+          c.beta = c.gamma > 0.0 ? tot / c.gamma : 0.0;
+          c.gamma = tot;
+          if (tot <= c.stop2) c.hit = 1;
+        } else {
+          c.beta = 0.0;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) *red.counter = 0u;
+}
+
+}  // namespace mdwf

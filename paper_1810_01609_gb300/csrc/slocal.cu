@@ -1,0 +1,222 @@
+// s-local kernels: the fifth-dimension operators D5 = b5 + c5 B, A5 = alpha + beta B and
+// A5^-1 on whole 5D columns (Sec. "Current State of the Art": the small dense diagonal
+// blocks of the domain-wall matrix), and the BLAS-1 steps of CG with FP64-accumulated,
+// fixed-order reductions (Sec. "Performance Measurement Method": all reductions in
+// double precision).
+//
+// Thread layout as in the hop kernels: a CTA owns ns 4D sites, thread (site_l, r, s).
+#include "mdwf_impl.cuh"
+#include "mdwf_kernels.h"
+
+namespace mdwf {
+
+// out = ca * chain(b) [+ cb * c]
+template <int P>
+__global__ void __launch_bounds__(MAXTHREADS) chain_kernel(const __grid_constant__ SLParams p) {
+  using C = typename PT<P>::C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Ls = p.b.Ls, nrhs = p.b.nrhs, W = Ls * nrhs, LsP = Ls + 1;
+  const int tid = threadIdx.x, site_l = tid / W, col = tid - site_l * W;
+  const long long x_cb = (long long)blockIdx.x * p.ns + site_l;
+  const bool active = x_cb < p.vh;
+  const int r = col / Ls, s = col - r * Ls, grp = site_l * nrhs + r;
+  C* tile = (C*)smem_raw;
+  if (active) {
+    C v[24];
+    load_site<P>(p.b, x_cb, col, v);
+#pragma unroll
+    for (int k = 0; k < 24; k++) tile[(grp * 24 + k) * LsP + s] = v[k];
+  }
+  __syncthreads();
+  const int nitems = p.ns * nrhs * 24;
+  for (int it = tid; it < nitems; it += blockDim.x) {
+    if ((long long)blockIdx.x * p.ns + (it / 24) / nrhs >= p.vh) continue;
+    chain_apply(p.chain, it % 24, tile + it * LsP, 1, Ls, (C)p.mf);
+  }
+  __syncthreads();
+  if (active) {
+    C v[24];
+    const C ca = (C)p.ca;
+#pragma unroll
+    for (int k = 0; k < 24; k++) v[k] = ca * tile[(grp * 24 + k) * LsP + s];
+    if (p.c.data) {
+      C w[24];
+      load_site<P>(p.c, x_cb, col, w);
+      const C cb = (C)p.cb;
+#pragma unroll
+      for (int k = 0; k < 24; k++) v[k] += cb * w[k];
+    }
+    store_site<P>(p.a, x_cb, col, v);
+  }
+}
+
+// a = ca * b + cb * c ; optional |a|^2
+template <int P>
+__global__ void __launch_bounds__(MAXTHREADS) axpby_kernel(const __grid_constant__ SLParams p) {
+  using C = typename PT<P>::C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Ls = p.b.Ls, nrhs = p.b.nrhs, W = Ls * nrhs;
+  const int tid = threadIdx.x, site_l = tid / W, col = tid - site_l * W;
+  const long long x_cb = (long long)blockIdx.x * p.ns + site_l;
+  double part = 0.0;
+  if (x_cb < p.vh) {
+    C v[24];
+    load_site<P>(p.b, x_cb, col, v);
+    const C ca = (C)p.ca;
+#pragma unroll
+    for (int k = 0; k < 24; k++) v[k] *= ca;
+    if (p.c.data) {
+      C w[24];
+      load_site<P>(p.c, x_cb, col, w);
+      const C cb = (C)p.cb;
+#pragma unroll
+      for (int k = 0; k < 24; k++) v[k] += cb * w[k];
+    }
+    if (p.red.mode != RED_NONE) {
+      C n = 0;
+#pragma unroll
+      for (int k = 0; k < 24; k++) n += v[k] * v[k];
+      part = (double)n;
+    }
+    if (p.a.data) store_site<P>(p.a, x_cb, col, v);
+  }
+  if (p.red.mode != RED_NONE) block_grid_reduce(p.red, part, (double*)smem_raw, Ls, p.ns);
+}
+
+// CG step: x += alpha p ; p = r + beta p ; phat = chain(p).   a = p, b = r, c = phat.
+template <int PX, int P>
+__global__ void __launch_bounds__(MAXTHREADS) cg_update_kernel(const __grid_constant__ SLParams p) {
+  using C = typename PT<P>::C;
+  using CX = typename PT<PX>::C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Ls = p.a.Ls, nrhs = p.a.nrhs, W = Ls * nrhs, LsP = Ls + 1;
+  const int tid = threadIdx.x, site_l = tid / W, col = tid - site_l * W;
+  const long long x_cb = (long long)blockIdx.x * p.ns + site_l;
+  const bool active = x_cb < p.vh;
+  const int r = col / Ls, s = col - r * Ls, grp = site_l * nrhs + r;
+  C* tile = (C*)smem_raw;
+  if (active) {
+    const double alpha = p.red.cg[r].alpha, beta = p.red.cg[r].beta;
+    C pv[24], rv[24];
+    load_site<P>(p.a, x_cb, col, pv);
+    if (alpha != 0.0) {
+      CX xv[24];
+      load_site<PX>(p.x, x_cb, col, xv);
+#pragma unroll
+      for (int k = 0; k < 24; k++) xv[k] += (CX)alpha * (CX)pv[k];
+      store_site<PX>(p.x, x_cb, col, xv);
+    }
+    load_site<P>(p.b, x_cb, col, rv);
+    const C bt = (C)beta;
+#pragma unroll
+    for (int k = 0; k < 24; k++) { pv[k] = rv[k] + bt * pv[k]; tile[(grp * 24 + k) * LsP + s] = pv[k]; }
+    store_site<P>(p.a, x_cb, col, pv);
+  }
+  __syncthreads();
+  const int nitems = p.ns * nrhs * 24;
+  for (int it = tid; it < nitems; it += blockDim.x) {
+    if ((long long)blockIdx.x * p.ns + (it / 24) / nrhs >= p.vh) continue;
+    chain_apply(p.chain, it % 24, tile + it * LsP, 1, Ls, (C)p.mf);
+  }
+  __syncthreads();
+  if (active) {
+    C v[24];
+#pragma unroll
+    for (int k = 0; k < 24; k++) v[k] = tile[(grp * 24 + k) * LsP + s];
+    store_site<P>(p.c, x_cb, col, v);
+  }
+}
+
+// a(PO) = [a +] b(PI); optionally b = 0
+template <int PO, int PI>
+__global__ void __launch_bounds__(MAXTHREADS) convert_kernel(const __grid_constant__ SLParams p) {
+  using CO = typename PT<PO>::C;
+  using CI = typename PT<PI>::C;
+  const int Ls = p.b.Ls, nrhs = p.b.nrhs, W = Ls * nrhs;
+  const int tid = threadIdx.x, site_l = tid / W, col = tid - site_l * W;
+  const long long x_cb = (long long)blockIdx.x * p.ns + site_l;
+  if (x_cb >= p.vh) return;
+  CI v[24];
+  load_site<PI>(p.b, x_cb, col, v);
+  CO o[24];
+  if (p.ca != 0.0) {
+    load_site<PO>(p.a, x_cb, col, o);
+#pragma unroll
+    for (int k = 0; k < 24; k++) o[k] += (CO)v[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 24; k++) o[k] = (CO)v[k];
+  }
+  store_site<PO>(p.a, x_cb, col, o);
+  if (p.cb != 0.0) {
+    CI z[24];
+#pragma unroll
+    for (int k = 0; k < 24; k++) z[k] = 0;
+    store_site<PI>(p.b, x_cb, col, z);
+  }
+}
+
+template <typename K>
+static cudaError_t go(K kern, const SLParams& p, int W, size_t smem, cudaStream_t st) {
+  static_assert(sizeof(SLParams) < 4000, "param size");
+  const long long blocks = (p.vh + p.ns - 1) / p.ns;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<(unsigned)blocks, p.ns * W, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+static size_t tile_bytes(int prec, const Field& f, int ns) {
+  return (size_t)ns * f.nrhs * 24 * (f.Ls + 1) * (prec == F64 ? 8 : 4);
+}
+
+cudaError_t launch_chain(int prec, const SLParams& p, cudaStream_t st) {
+  const int W = p.b.nrhs * p.b.Ls;
+  const size_t smem = tile_bytes(prec, p.b, p.ns);
+  switch (prec) {
+    case F64: return go(chain_kernel<F64>, p, W, smem, st);
+    case F32: return go(chain_kernel<F32>, p, W, smem, st);
+    case F16: return go(chain_kernel<F16>, p, W, smem, st);
+    case BF16: return go(chain_kernel<BF16>, p, W, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_axpby(int prec, const SLParams& p, cudaStream_t st) {
+  const int W = p.b.nrhs * p.b.Ls;
+  const size_t smem = 2 * (size_t)p.ns * W * sizeof(double) + 16;
+  switch (prec) {
+    case F64: return go(axpby_kernel<F64>, p, W, smem, st);
+    case F32: return go(axpby_kernel<F32>, p, W, smem, st);
+    case F16: return go(axpby_kernel<F16>, p, W, smem, st);
+    case BF16: return go(axpby_kernel<BF16>, p, W, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_cg_update(int prec_x, int prec, const SLParams& p, cudaStream_t st) {
+  const int W = p.a.nrhs * p.a.Ls;
+  const size_t smem = tile_bytes(prec, p.a, p.ns);
+  if (prec == F64 && prec_x == F64) return go(cg_update_kernel<F64, F64>, p, W, smem, st);
+  if (prec_x == F32) {
+    switch (prec) {
+      case F32: return go(cg_update_kernel<F32, F32>, p, W, smem, st);
+      case F16: return go(cg_update_kernel<F32, F16>, p, W, smem, st);
+      case BF16: return go(cg_update_kernel<F32, BF16>, p, W, smem, st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_convert(int po, int pi, const SLParams& p, cudaStream_t st) {
+  const int W = p.b.nrhs * p.b.Ls;
+#define CV(A, B) if (po == A && pi == B) return go(convert_kernel<A, B>, p, W, 0, st);
+  CV(F64, F64) CV(F64, F32) CV(F64, F16) CV(F64, BF16)
+  CV(F32, F64) CV(F16, F64) CV(BF16, F64) CV(F32, F32)
+#undef CV
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace mdwf

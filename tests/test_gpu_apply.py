@@ -1,0 +1,176 @@
+"""GPU parity of the operator kernels (C ABI mdwf_apply / mdwf_pack / mdwf_unpack) against
+the FP64 oracle on the same seeded inputs.  Tolerances: relative 2-norm difference of the
+whole output, FP64 1e-13, FP32 1e-6, F16 (+norm) 2e-3, BF16 8e-3 (8 significant bits:
+unit roundoff 2^-9 on input and output)."""
+import numpy as np
+import pytest
+
+import inputs
+from oracle import dirac, storage
+from oracle.dirac import MobiusParams
+from gpu_common import lib, rel, to_dev, to_host, parity_of, torch
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-13, "f32": 1e-6, "f16": 2e-3, "bf16": 8e-3}
+# (dims, Ls, nrhs): several tiles, ragged last tile for ns >= 16 (Vh = 72 = 8 * 9)
+CASES = [((4, 4, 4, 4), 8, 1), ((6, 2, 2, 6), 6, 1), ((4, 4, 4, 4), 5, 3)]
+
+
+def _setup(dims, Ls, nrhs, mf=0.05, seed=1, eps=0.3, recon=18):
+    m = lib()
+    U = inputs.gauge_links(dims, eps, seed)
+    ctx = m.Context(dims, Ls, mf=mf, recon=recon)
+    ctx.load_gauge(U)
+    psi = inputs.gaussian_spinor5d(dims, Ls, seed + 100, nrhs=nrhs)
+    p = MobiusParams(Ls=Ls, mf=mf)
+    return m, ctx, U, dirac.boundary_links(U, -1.0), psi, p
+
+
+def _gpu_apply(m, ctx, op, prec, psi, nrhs):
+    nb = ctx.field_bytes(prec, nrhs)
+    fin = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    fout = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    d = to_dev(psi)
+    m.mdwf_pack(ctx.h, d, fin, m.PRECS[prec], nrhs)
+    m.mdwf_apply(ctx.h, m.OP[op], m.PRECS[prec], fin, fout, nrhs)
+    out = torch.zeros_like(d)
+    m.mdwf_unpack(ctx.h, fout, out, m.PRECS[prec], nrhs)
+    torch.cuda.synchronize()
+    return to_host(out)
+
+
+def _oracle(op, Ub, psi, p, par):
+    e = lambda f: dirac.on_parity(f, par, 0)
+    o = lambda f: dirac.on_parity(f, par, 1)
+    if op == "HOP_EO":
+        return e(dirac.hop(Ub, o(psi)))
+    if op == "HOP_OE":
+        return o(dirac.hop(Ub, e(psi)))
+    if op == "HOP_EO_DAG":
+        return e(dirac.hop(Ub, o(psi), dagger=True))
+    if op == "HOP_OE_DAG":
+        return o(dirac.hop(Ub, e(psi), dagger=True))
+    if op in ("D5", "M5", "M5INV"):
+        return dirac.s_op(p, {"D5": "D5", "M5": "A5", "M5INV": "A5inv"}[op], psi)
+    if op in ("D5_DAG", "M5_DAG", "M5INV_DAG"):
+        return dirac.s_op(p, {"D5_DAG": "D5", "M5_DAG": "A5", "M5INV_DAG": "A5inv"}[op], psi, dagger=True)
+    if op == "HOP_EO_M5INV":
+        return e(dirac.s_op(p, "A5inv", dirac.hop(Ub, o(psi))))
+    if op == "HOP_OE_M5INV":
+        return o(dirac.s_op(p, "A5inv", dirac.hop(Ub, e(psi))))
+    if op == "MPC":
+        return dirac.mpc(Ub, o(psi), p)
+    if op == "MPC_DAG":
+        return dirac.mpc_dag(Ub, o(psi), p)
+    if op == "MDAGM":
+        return dirac.mpc_dag(Ub, dirac.mpc(Ub, o(psi), p), p)
+    if op == "FULL_D":
+        return dirac.mobius(Ub, psi, p)
+    if op == "FULL_D_DAG":
+        return dirac.mobius(Ub, psi, p, dagger=True)
+    raise ValueError(op)
+
+
+def _mask(op, par, shape):
+    """Which parity halves an op writes (the rest of `out` stays zero)."""
+    if op in ("HOP_EO", "HOP_EO_DAG", "HOP_EO_M5INV"):
+        keep = par == 0
+    elif op in ("HOP_OE", "HOP_OE_DAG", "HOP_OE_M5INV", "MPC", "MPC_DAG", "MDAGM"):
+        keep = par == 1
+    else:
+        return None
+    return keep
+
+
+ALL_OPS = ["HOP_EO", "HOP_OE", "HOP_EO_DAG", "HOP_OE_DAG", "D5", "D5_DAG", "M5", "M5_DAG", "M5INV",
+           "M5INV_DAG", "HOP_EO_M5INV", "HOP_OE_M5INV", "MPC", "MPC_DAG", "MDAGM", "FULL_D", "FULL_D_DAG"]
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
+def test_apply_parity(case, prec, monkeypatch):
+    dims, Ls, nrhs = case
+    if dims == (6, 2, 2, 6):
+        monkeypatch.setenv("MDWF_FORCE_NS", "16")
+    m, ctx, U, Ub, psi, p = _setup(dims, Ls, nrhs)
+    par = parity_of(dims)
+    for op in ALL_OPS:
+        got = _gpu_apply(m, ctx, op, prec, psi, nrhs)
+        ref = np.stack([_oracle(op, Ub, psi[r], p, par) for r in range(nrhs)])
+        keep = _mask(op, par, ref.shape)
+        if keep is not None:
+            # untouched half stays zero
+            other = np.broadcast_to((~keep)[None, None, ..., None, None], got.shape)
+            assert not np.any(got[other]), op
+        err = rel(got, ref)
+        assert err <= TOL[prec], (op, prec, err)
+
+
+def test_recon12_matches_recon18():
+    m = lib()
+    dims, Ls = (4, 4, 4, 4), 6
+    for prec in ("f64", "f32", "f16"):
+        outs = []
+        for recon in (18, 12):
+            m_, ctx, U, Ub, psi, p = _setup(dims, Ls, 1, recon=recon)
+            outs.append(_gpu_apply(m, ctx, "FULL_D", prec, psi, 1))
+        assert rel(outs[1], outs[0]) <= {"f64": 1e-14, "f32": 1e-6, "f16": 2e-3}[prec]
+
+
+def _internal_half_f16(raw, ctx, nrhs, parity):
+    """Decode the documented internal F16 layout of one parity half into
+    (halves [vh, nrhs, Ls, 24] in [colour][spin][re,im] order, norms [vh, nrhs, Ls])."""
+    X, Y, Z, T = ctx.dims
+    vh = X * Y * Z * T // 2
+    Ls = ctx.Ls
+    W = nrhs * Ls
+    dbytes = vh * 3 * W * 16
+    data = raw[parity * dbytes:(parity + 1) * dbytes].view(np.float16).reshape(vh, 3, nrhs, Ls, 8)
+    h = np.transpose(data, (0, 2, 3, 1, 4)).reshape(vh, nrhs, Ls, 24)
+    nb = vh * W * 4
+    norms = raw[2 * dbytes + parity * nb: 2 * dbytes + (parity + 1) * nb].view(np.float32).reshape(vh, nrhs, Ls)
+    return h, norms
+
+
+def test_pack_f16_bit_exact_and_roundtrip():
+    m = lib()
+    dims, Ls, nrhs = (4, 4, 2, 4), 4, 2
+    ctx = m.Context(dims, Ls)
+    psi = inputs.gaussian_spinor5d(dims, Ls, 7, nrhs=nrhs)
+    psi[0, 1, 0, 0, 0, 0] = 0.0        # an all-zero 5D site
+    psi[1, 2, 1] *= 1e-30              # tiny magnitudes
+    d = to_dev(psi)
+    nb = ctx.field_bytes("f16", nrhs)
+    buf = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    m.mdwf_pack(ctx.h, d, buf, m.PRECS["f16"], nrhs)
+    raw = buf.cpu().numpy()
+    X, Y, Z, T = dims
+    par = parity_of(dims)
+    for parity in (0, 1):
+        h, n = _internal_half_f16(raw, ctx, nrhs, parity)
+        # site order of the half: x_cb = full index // 2 over sites of this parity
+        t, z, y, x = np.nonzero(par == parity)
+        order = np.argsort(((t * Z + z) * Y + y) * X + x)
+        t, z, y, x = t[order], z[order], y[order], x[order]
+        sites = psi[:, :, t, z, y, x]                 # [nrhs, Ls, vh, spin, colour]
+        reals = np.stack([sites.real, sites.imag], -1)  # [..., spin, colour, 2]
+        reals = np.transpose(reals, (2, 0, 1, 4, 3, 5)).reshape(len(t), nrhs, Ls, 24)
+        eh, en = storage.quantize_f16(reals)
+        assert np.array_equal(n, en)
+        assert np.array_equal(h.view(np.uint16), eh.view(np.uint16))
+    # FP64 round trip is bit-exact
+    nb64 = ctx.field_bytes("f64", nrhs)
+    b64 = torch.zeros(nb64, dtype=torch.uint8, device="cuda")
+    m.mdwf_pack(ctx.h, d, b64, 0, nrhs)
+    back = torch.zeros_like(d)
+    m.mdwf_unpack(ctx.h, b64, back, 0, nrhs)
+    assert np.array_equal(to_host(back), psi)
+    # BF16 values are the nearest-even 8-bit roundings
+    nbb = ctx.field_bytes("bf16", nrhs)
+    bb = torch.zeros(nbb, dtype=torch.uint8, device="cuda")
+    m.mdwf_pack(ctx.h, d, bb, 3, nrhs)
+    m.mdwf_unpack(ctx.h, bb, back, 3, nrhs)
+    got = to_host(back)
+    assert np.array_equal(got.real, storage.round_bf16(psi.real))
+    assert np.array_equal(got.imag, storage.round_bf16(psi.imag))

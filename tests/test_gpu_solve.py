@@ -1,0 +1,89 @@
+"""GPU solves through the C ABI against the FP64 oracle solve: the plain FP64 CG and the
+mixed-precision reliable-update CG (F32 / F16+norm / BF16 inner storage) must reach a
+true FP64 relative residual <= 1e-10 and agree with the oracle solution to 1e-8."""
+import numpy as np
+import pytest
+
+import inputs
+from oracle import dirac, solve, hadron
+from oracle.dirac import MobiusParams
+from gpu_common import lib, rel, to_dev, to_host, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _problem(dims=(4, 4, 4, 4), Ls=8, mf=0.05, eps=0.2, seed=1):
+    U = inputs.gauge_links(dims, eps, seed)
+    p = MobiusParams(Ls=Ls, mf=mf)
+    Ub = dirac.boundary_links(U, -1.0)
+    b = inputs.gaussian_spinor5d(dims, Ls, seed + 50)
+    xo, _, _ = solve.solve_eo(Ub, b, p, tol=1e-12)
+    return U, Ub, p, b, xo
+
+
+@pytest.mark.parametrize("sloppy", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_solve_matches_oracle(sloppy, use_graph):
+    m = lib()
+    dims, Ls, mf = (4, 4, 4, 4), 8, 0.05
+    U, Ub, p, b, xo = _problem(dims, Ls, mf)
+    ctx = m.Context(dims, Ls, mf=mf)
+    ctx.load_gauge(U)
+    x, info = ctx.solve(to_dev(b), tol=1e-10, sloppy=sloppy, use_graph=use_graph)
+    x = to_host(x)
+    assert info.status == 0
+    assert info.true_residual <= 1e-10
+    assert solve.residual_full(Ub, b, x, p) <= 1e-9
+    assert abs(info.full_residual - solve.residual_full(Ub, b, x, p)) < 1e-12
+    assert rel(x, xo) <= 1e-8
+    if sloppy != "f64":
+        assert info.reliable_updates >= 1
+
+
+def test_solve_host_buffers_and_ragged_lattice():
+    m = lib()
+    dims, Ls, mf = (6, 2, 2, 6), 6, 0.1
+    U, Ub, p, b, xo = _problem(dims, Ls, mf, eps=0.4, seed=3)
+    ctx = m.Context(dims, Ls, mf=mf)
+    ctx.load_gauge(U)
+    x, info = ctx.solve(b, tol=1e-10, sloppy="f16")   # numpy -> host location path
+    assert info.true_residual <= 1e-10
+    assert rel(x, xo) <= 1e-8
+
+
+def test_solve_multi_matches_single():
+    m = lib()
+    dims, Ls, mf = (4, 4, 4, 4), 6, 0.05
+    U = inputs.gauge_links(dims, 0.3, 5)
+    Ub = dirac.boundary_links(U, -1.0)
+    p = MobiusParams(Ls=Ls, mf=mf)
+    nrhs = 4
+    b = inputs.gaussian_spinor5d(dims, Ls, 77, nrhs=nrhs)
+    b[2] *= 1e-3    # right-hand sides of very different scale converge independently
+    ctx = m.Context(dims, Ls, mf=mf)
+    ctx.load_gauge(U)
+    for sloppy in ("f64", "f16"):
+        x, infos = ctx.solve_multi(to_dev(b), tol=1e-10, sloppy=sloppy)
+        x = to_host(x)
+        for r in range(nrhs):
+            assert infos[r].true_residual <= 1e-10, (sloppy, r, infos[r].true_residual)
+            xo, _, _ = solve.solve_eo(Ub, b[r], p, tol=1e-12)
+            assert rel(x[r], xo) <= 1e-8, (sloppy, r)
+
+
+def test_zero_source_and_bad_args():
+    m = lib()
+    dims, Ls = (4, 4, 4, 4), 4
+    ctx = m.Context(dims, Ls)
+    ctx.load_gauge(inputs.gauge_links(dims, 0.2, 1))
+    b = np.zeros(ctx.shape5d(), dtype=np.complex128)
+    x, info = ctx.solve(b)
+    assert info.status == 0 and not np.any(x)
+    with pytest.raises(m.MdwfError) as e:
+        ctx.solve(b, tol=-1.0)
+    assert e.value.code == m.MDWF_ERR_ARG
+    # maxiter too small: not converged, solution still written
+    b[0, 0, 0, 0, 0, 0, 0] = 1.0
+    x, info = ctx.solve(b, maxiter=5, check_interval=5)
+    assert info.status == m.MDWF_ERR_NOT_CONVERGED and info.iterations == 5
+    assert np.any(x)
