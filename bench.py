@@ -1,0 +1,354 @@
+"""Benchmark of the MDWF propagator solve on GB300.
+
+Workload (default): 16^3 x 32 lattice, Ls = 12, Moebius b5 = 1.5, c5 = 0.5, M5 = 1.3,
+m_f = 0.02, synthetic links exp(i 0.4 H) reunitarised (Philox seed 2), one spin-colour
+point source at the origin.  One step = the point-source propagator column through the
+library's public calls: 4D source -> 5D source (Pauli-Villars injection), mixed-precision
+(F16 + norm storage, FP32 arithmetic, FP64 reliable updates) even-odd CG on the normal
+equations to a true FP64 relative residual of 1e-10, and the 4D projection.
+
+Reported: value = algorithmic HBM GB/s of the whole step (bytes the library's kernels must
+move, counted by the library, divided by the step's device time), the mixed and the plain
+FP64 solve times to 1e-10 and their ratio, the roofline of the dominant kernel (the fused
+hop + M5^-1 kernel, timed alone with an L2 flush before every launch), end-to-end numbers
+through host buffers, SM clocks during the timed region and the FP64 CPU oracle timed on
+the host cores.
+
+--impl reference runs the oracle (the FP64 numpy reference of the method) on the host
+cores on a bounded sample of the same workload and prints the same JSON line.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: dims (X,Y,Z,T), Ls, mf, eps, seed
+    "16^3x32_Ls12": ((16, 16, 16, 32), 12, 0.02, 0.4, 2),
+    "24^3x64_Ls10": ((24, 24, 24, 64), 10, 0.01, 0.5, 3),
+    "4^4_Ls8": ((4, 4, 4, 4), 8, 0.05, 0.2, 1),
+}
+METRIC = "MDWF Dslash HBM GB/s (% of peak); solve time to 1e-10, mixed vs FP64"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.samples = []
+        self.proc = None
+        self.idx = gpu_index
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def cpu_oracle_sample(dims, Ls, mf, eps, seed, budget_s=20.0):
+    """Time CGNR iterations of the FP64 numpy oracle on the host cores (bounded sample)."""
+    import inputs
+    from oracle import dirac
+    from oracle.dirac import MobiusParams
+    U = inputs.gauge_links(dims, eps, seed)
+    p = MobiusParams(Ls=Ls, mf=mf)
+    Ub = dirac.boundary_links(U, -1.0)
+    par = dirac.parity_mask(dims)
+    x = dirac.on_parity(inputs.gaussian_spinor5d(dims, Ls, seed + 100), par, 1)
+    t0 = time.perf_counter()
+    its = 0
+    while True:
+        q = dirac.mpc(Ub, x, p)                 # one CG iteration = M_pc and M_pc^+ applies
+        x = dirac.mpc_dag(Ub, q, p) * 1e-1
+        its += 1
+        if time.perf_counter() - t0 >= budget_s or its >= 50:
+            break
+    dt = time.perf_counter() - t0
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count()
+    return its, dt, cores
+
+
+def per_iteration_bytes(dims, Ls, nrhs=1):
+    """Algorithmic bytes of one mixed (F16) CG iteration, the library's own count:
+    K1 hop (in, out, links), K2 hop (+centre), K3 hop, K4 hop (+centre, r read+write),
+    cg_update (x F32 read+write, p read+write, r read, phat write)."""
+    vh = dims[0] * dims[1] * dims[2] * dims[3] // 2
+    f16 = vh * Ls * nrhs * 52.0
+    f32 = vh * Ls * nrhs * 96.0
+    links = vh * 8 * 18 * 2.0
+    return (2 * f16 + links) + (3 * f16 + links) + (2 * f16 + links) + (4 * f16 + links) + (2 * f32 + 4 * f16)
+
+
+def run_reference(args, wl):
+    dims, Ls, mf, eps, seed = WORKLOADS[wl]
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    steps = []
+    cores = None
+    for i in range(args.warmup + args.steps):
+        its, dt, cores = cpu_oracle_sample(dims, Ls, mf, eps, seed, budget_s=args.ref_budget)
+        if i >= args.warmup:
+            steps.append((its, dt))
+    its = sum(s[0] for s in steps)
+    dt = sum(s[1] for s in steps)
+    gbs = its * per_iteration_bytes(dims, Ls) / dt / 1e9
+    sample = "%d CGNR iterations (M_pc + M_pc^+ applies) of the FP64 numpy oracle on %s, Ls=%d" % (
+        its, "x".join(map(str, dims)), Ls)
+    out = {"metric": METRIC, "value": gbs, "unit": "GB/s", "impl": "reference", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / len(steps) * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": wl, "lattice": list(dims), "Ls": Ls, "mf": mf},
+           "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def kernel_only(args, m, ctx, dims, Ls, seed, stream):
+    import torch
+    import inputs
+    prec = m.PRECS[args.sloppy]
+    nb = ctx.field_bytes(args.sloppy, 1)
+    fin = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    fout = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    src = torch.from_numpy(inputs.gaussian_spinor5d(dims, Ls, seed + 100)).cuda()
+    m.mdwf_pack(ctx.h, src, fin, prec, 1, stream)
+    for _ in range(args.kernel_launches):
+        m.mdwf_apply(ctx.h, m.OP[args.op], prec, fin, fout, 1, stream)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_only": args.op, "launches": args.kernel_launches, "tune": ctx.tune_entries()}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="16^3x32_Ls12", choices=sorted(WORKLOADS))
+    ap.add_argument("--sloppy", default="f16", choices=["f16", "bf16", "f32"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--kernel-launches", type=int, default=20)
+    ap.add_argument("--ref-budget", type=float, default=20.0)
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="only launch the fused hop + M5^-1 kernel a few times (for ncu captures)")
+    ap.add_argument("--op", default="HOP_OE_M5INV")
+    args = ap.parse_args()
+    wl = args.workload
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import inputs
+    import paper_1810_01609_gb300 as m
+
+    dims, Ls, mf, eps, seed = WORKLOADS[wl]
+    X, Y, Z, T = dims
+    V = X * Y * Z * T
+    U = inputs.gauge_links(dims, eps, seed)
+    ctx = m.Context(dims, Ls, mf=mf)
+    ctx.load_gauge(U)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)   # graphs cannot be captured on the legacy default stream
+    if args.kernel_only:
+        return kernel_only(args, m, ctx, dims, Ls, seed, stream)
+    b4 = torch.from_numpy(inputs.point_source4d(dims, 0, 0)).cuda().reshape((1,) + ctx.shape4d())
+
+    def step(b4d, sloppy):
+        eta = ctx.make_source_4d(b4d, nrhs=1, stream=stream)
+        x, info = ctx.solve(eta[0], sloppy=sloppy, tol=1e-10, stream=stream)
+        q = ctx.project_4d(x.reshape((1,) + x.shape), nrhs=1, stream=stream)
+        return q, info
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(b4, args.sloppy)
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    bytes0, launches0 = ctx.algorithmic_bytes(), ctx.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        q, info = step(b4, args.sloppy)
+        infos.append(info)
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    step_bytes = (ctx.algorithmic_bytes() - bytes0) / args.steps
+    launches = ctx.launch_count() - launches0
+    ms_step = ms / args.steps
+    if dist is not None:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * step_bytes / (ms_step * 1e-3) / 1e9
+
+    # plain FP64 solve of the same source (same accuracy), once
+    fp64 = None
+    if not args.no_fp64:
+        eta = ctx.make_source_4d(b4, nrhs=1, stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x64, i64 = ctx.solve(eta[0], sloppy="f64", tol=1e-10, stream=stream)
+        torch.cuda.synchronize()
+        fp64 = {"ms": (time.perf_counter() - t0) * 1e3, "iterations": i64.iterations,
+                "true_residual": i64.true_residual}
+
+    # roofline leg: the fused hop + M5^-1 kernel (F16) timed alone, L2 flushed before each launch
+    prec = m.PRECS[args.sloppy]
+    nb = ctx.field_bytes(args.sloppy, 1)
+    fin = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    fout = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    src = torch.from_numpy(inputs.gaussian_spinor5d(dims, Ls, seed + 100)).cuda()
+    m.mdwf_pack(ctx.h, src, fin, prec, 1, stream)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    op = m.OP["HOP_OE_M5INV"]
+    for _ in range(3):
+        m.mdwf_apply(ctx.h, op, prec, fin, fout, 1, stream)
+    kt = []
+    for _ in range(args.kernel_launches):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        m.mdwf_apply(ctx.h, op, prec, fin, fout, 1, stream)
+        b.record(stream)
+        b.synchronize()
+        kt.append(a.elapsed_time(b))
+    kms = float(np.mean(kt))
+    vh = V // 2
+    site = {"f16": 52.0, "bf16": 48.0, "f32": 96.0}[args.sloppy]
+    link = {"f16": 2, "bf16": 2, "f32": 4}[args.sloppy] * 18.0
+    kbytes = vh * Ls * 2 * site + vh * 8 * link
+    peak, peak_kind = peaks()
+    achieved = kbytes / (kms * 1e-3) / 1e9
+    del flush
+
+    # end to end through host buffers: pinned 4D source in, 4D propagator column out
+    b4h = b4.cpu().pin_memory()
+    qh = torch.empty((1,) + ctx.shape4d(), dtype=torch.complex128).pin_memory()
+    torch.cuda.synchronize()
+    ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_bytes0 = ctx.algorithmic_bytes()
+    ee0.record(stream)
+    for _ in range(args.steps):
+        bd = b4h.to("cuda", non_blocking=True)
+        q, _ = step(bd, args.sloppy)
+        qh.copy_(q, non_blocking=True)
+    ee1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = ee0.elapsed_time(ee1) / args.steps
+    e2e_val = world * (ctx.algorithmic_bytes() - e2e_bytes0) / args.steps / (e2e_ms * 1e-3) / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        its, dt, cores = cpu_oracle_sample(dims, Ls, mf, eps, seed)
+        cgbs = its * per_iteration_bytes(dims, Ls) / dt / 1e9
+        cpu = {"value": cgbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
+               "sample": "%d CGNR iterations (M_pc + M_pc^+) of the FP64 numpy oracle on %s, Ls=%d, %.1f s; "
+                         "GB/s = the GPU step's algorithmic bytes per CG iteration x iterations / time"
+                         % (its, "x".join(map(str, dims)), Ls, dt)}
+
+    mixed_ms = float(np.mean([i.time_ms for i in infos]))
+    out = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f16+f32 (inner), f64 (reliable updates, reductions)",
+        "data": "synthetic",
+        "config": {"workload": wl, "lattice": list(dims), "Ls": Ls, "mf": mf, "b5": 1.5, "c5": 0.5, "M5": 1.3,
+                   "link_eps": eps, "seed": seed, "source": "point (spin 0, colour 0, origin)",
+                   "sloppy": args.sloppy, "tol": 1e-10,
+                   "l2": "step working set > L2; roofline kernel launches preceded by a 512 MB L2 flush",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "solve": {"mixed_ms": mixed_ms, "iterations": infos[-1].iterations,
+                  "reliable_updates": infos[-1].reliable_updates, "true_residual": infos[-1].true_residual,
+                  "full_residual": infos[-1].full_residual,
+                  "fp64_ms": fp64["ms"] if fp64 else None, "fp64_iterations": fp64["iterations"] if fp64 else None,
+                  "fp64_true_residual": fp64["true_residual"] if fp64 else None,
+                  "speedup_vs_fp64": (fp64["ms"] / mixed_ms) if fp64 else None},
+        "roofline": {"kernel": "fused hop + M5^-1 (HOP_OE_M5INV, %s)" % args.sloppy, "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "bytes_per_launch": kbytes, "ms_per_launch": kms},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": "GB/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(b4h.numel() * 16), "d2h_bytes_per_step": int(qh.numel() * 16)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -216,6 +216,11 @@ int mdwf_tune_entry(const mdwf_ctx* ctx, int i, char* key, int keylen, int* site
 
 /* Number of kernels this context has launched so far (all streams). */
 long long mdwf_launch_count(const mdwf_ctx* ctx);
+/* Algorithmic HBM bytes of every kernel this context has launched so far: each field a
+ * kernel reads or writes counted once per 5D site (F64 192 B, F32 96 B, F16 48 B + 4 B
+ * norm, BF16 48 B), links once per launch (8 per output 4D site, 18 or 12 reals), user
+ * complex128 fields at 192 B per 5D site. */
+double mdwf_algorithmic_bytes(const mdwf_ctx* ctx);
 
 /* Name of a status code. */
 const char* mdwf_strerror(int status);

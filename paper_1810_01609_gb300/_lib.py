@@ -77,6 +77,7 @@ _SIGS = {
     "mdwf_tune_entries": (_I, [_V, ctypes.POINTER(_I)]),
     "mdwf_tune_entry": (_I, [_V, _I, ctypes.c_char_p, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "mdwf_launch_count": (ctypes.c_longlong, [_V]),
+    "mdwf_algorithmic_bytes": (ctypes.c_double, [_V]),
     "mdwf_strerror": (ctypes.c_char_p, [_I]),
     "mdwf_last_error": (ctypes.c_char_p, []),
 }
@@ -235,6 +236,10 @@ def mdwf_tune_entries(ctx):
 
 def mdwf_launch_count(ctx):
     return load().mdwf_launch_count(ctx)
+
+
+def mdwf_algorithmic_bytes(ctx):
+    return load().mdwf_algorithmic_bytes(ctx)
 
 
 def mdwf_last_error():

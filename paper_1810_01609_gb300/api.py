@@ -117,3 +117,6 @@ class Context:
 
     def launch_count(self):
         return L.mdwf_launch_count(self.h)
+
+    def algorithmic_bytes(self):
+        return L.mdwf_algorithmic_bytes(self.h)

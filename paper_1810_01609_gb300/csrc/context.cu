@@ -82,7 +82,9 @@ struct mdwf_ctx {
   std::string tune_file;
   // graphs
   std::map<std::string, cudaGraphExec_t> graphs;
+  std::map<std::string, double> graph_bytes;  // algorithmic bytes of one replay
   long long launches = 0;
+  double bytes = 0.0;  // algorithmic HBM bytes of every kernel launched (see site_bytes)
 };
 
 namespace {
@@ -172,6 +174,13 @@ int ws_half(mdwf_ctx* c, const std::string& name, int prec, int nrhs, Field* f) 
   f->norm = prec_norm(prec) ? (float*)((char*)p + ((d + 255) & ~(size_t)255)) : nullptr;
   f->nrhs = nrhs; f->Ls = c->Ls; f->vh = c->vh;
   return MDWF_SUCCESS;
+}
+// algorithmic bytes of one 5D site of a field in storage precision prec
+double site_bytes(int prec) { return prec == F64 ? 192.0 : prec == F32 ? 96.0 : prec == F16 ? 52.0 : 48.0; }
+double half_bytes(const Field& f, int prec) { return (double)f.vh * f.nrhs * f.Ls * site_bytes(prec); }
+// links: 18 (or 12) reals per link, 8 links per output 4D site
+double gauge_bytes(const mdwf_ctx* c, int prec) {
+  return (double)c->vh * 8 * (c->prm.gauge_recon == 12 ? 12 : 18) * prec_gsize(prec);
 }
 size_t field_bytes_of(const Field& f, int prec) {
   return (size_t)f.vh * prec_nc(prec) * f.nrhs * f.Ls * 16;
@@ -399,6 +408,8 @@ int hop(mdwf_ctx* c, int prec, bool dag, const Field& in, const Field& out, int 
     }
     cudaError_t err = launch_hop(prec, dag, r12, e.on, q, st);
     c->launches++;
+    c->bytes += half_bytes(in, prec) + gauge_bytes(c, prec) + (q.has_center ? half_bytes(e.center, prec) : 0.0) +
+                (q.axpy_r ? 2.0 * half_bytes(e.raxpy, prec) : half_bytes(out, prec));
     if (err != cudaSuccess) { set_err("launch_hop", err); return MDWF_ERR_CUDA; }
     return MDWF_SUCCESS;
   };
@@ -426,6 +437,7 @@ int sl_chain(mdwf_ctx* c, int prec, const Field& out, const Field& in, const SCh
     q.ns = ns;
     cudaError_t err = launch_chain(prec, q, st);
     c->launches++;
+    c->bytes += half_bytes(in, prec) * (add ? 3.0 : 2.0);
     if (err != cudaSuccess) { set_err("launch_chain", err); return MDWF_ERR_CUDA; }
     return MDWF_SUCCESS;
   };
@@ -452,6 +464,7 @@ int sl_axpby(mdwf_ctx* c, int prec, const Field* a, const Field& b, double ca, c
   }
   cudaError_t err = launch_axpby(prec, p, st);
   c->launches++;
+  c->bytes += half_bytes(b, prec) * (1.0 + (cfield ? 1.0 : 0.0) + (a ? 1.0 : 0.0));
   if (err != cudaSuccess) { set_err("launch_axpby", err); return MDWF_ERR_CUDA; }
   return MDWF_SUCCESS;
 }
@@ -465,6 +478,7 @@ int sl_convert(mdwf_ctx* c, int po, const Field& out, int pi, const Field& in, b
   p.ns = ns_default(W);
   cudaError_t err = launch_convert(po, pi, p, st);
   c->launches++;
+  c->bytes += half_bytes(in, pi) * (zero_in ? 2.0 : 1.0) + half_bytes(out, po) * (accumulate ? 2.0 : 1.0);
   if (err != cudaSuccess) { set_err("launch_convert", err); return MDWF_ERR_CUDA; }
   return MDWF_SUCCESS;
 }
@@ -593,6 +607,7 @@ int cg_iteration(mdwf_ctx* c, const CGSet& v, cudaStream_t st) {
     qq.ns = ns;
     cudaError_t err = launch_cg_update(v.prec_x, P, qq, st);
     c->launches++;
+    c->bytes += 2.0 * half_bytes(v.x, v.prec_x) + 4.0 * half_bytes(v.p, P);
     if (err != cudaSuccess) { set_err("launch_cg_update", err); return MDWF_ERR_CUDA; }
     return MDWF_SUCCESS;
   };
@@ -627,7 +642,10 @@ int run_iterations(mdwf_ctx* c, const CGSet& v, int n, bool use_graph, cudaStrea
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     int s = MDWF_SUCCESS;
     const long long before = c->launches;
+    const double bytes_before = c->bytes;
     for (int i = 0; i < n && s == MDWF_SUCCESS; i++) s = cg_iteration(c, v, st);
+    c->graph_bytes[key] = c->bytes - bytes_before;
+    c->bytes = bytes_before;
     cudaError_t e = cudaStreamEndCapture(st, &graph);
     if (s != MDWF_SUCCESS) return s;
     CK(e);
@@ -639,6 +657,7 @@ int run_iterations(mdwf_ctx* c, const CGSet& v, int n, bool use_graph, cudaStrea
   }
   CK(cudaGraphLaunch(it->second, st));
   c->launches += 5LL * n;
+  c->bytes += c->graph_bytes[key];
   return MDWF_SUCCESS;
 }
 
@@ -970,6 +989,7 @@ int mdwf_pack(mdwf_ctx* c, const double* user5d, void* internal, int prec, int n
   }
   CK(launch_pack(prec, p, (cudaStream_t)stream));
   c->launches++;
+  c->bytes += (double)2 * c->vh * nrhs * c->Ls * (192.0 + site_bytes(prec));
   return MDWF_SUCCESS;
 }
 
@@ -983,6 +1003,7 @@ int mdwf_unpack(mdwf_ctx* c, const void* internal, double* user5d, int prec, int
   }
   CK(launch_unpack(prec, p, (cudaStream_t)stream));
   c->launches++;
+  c->bytes += (double)2 * c->vh * nrhs * c->Ls * (192.0 + site_bytes(prec));
   return MDWF_SUCCESS;
 }
 
@@ -1267,5 +1288,7 @@ int mdwf_tune_entry(const mdwf_ctx* c, int i, char* key, int keylen, int* ns, do
 }
 
 long long mdwf_launch_count(const mdwf_ctx* c) { return c ? c->launches : 0; }
+
+double mdwf_algorithmic_bytes(const mdwf_ctx* c) { return c ? c->bytes : 0.0; }
 
 }  // extern "C"

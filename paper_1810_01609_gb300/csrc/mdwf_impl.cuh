@@ -240,7 +240,7 @@ __device__ __forceinline__ void chain_apply(const SChain& ch, int comp, C* y, in
 #pragma unroll
   for (int i = 0; i < 2; i++) {
     if (ch.op[i].kind == SOP_NONE) continue;
-    const bool up = (lower != (bool)ch.op[i].dag);  // B: P_- up; B^+: P_+ up
+    const bool up = (!lower) != (bool)ch.op[i].dag;  // B: P_- up; B^+: P_+ up
     sop_apply(ch.op[i], up, y, st, Ls, mf);
   }
 }
