@@ -387,17 +387,29 @@ int hop(mdwf_ctx* c, int prec, bool dag, const Field& in, const Field& out, int 
   p.red = red;
   const bool r12 = c->prm.gauge_recon == 12;
   const int W = in.nrhs * in.Ls;
+  // MDWF_TC=1 selects the tensor-core kernel (one warp per 4D site) for F16 / BF16 storage
+  const char* use_tc = getenv("MDWF_TC");
+  const bool tc = (use_tc && use_tc[0] == '1') && hop_tc_supported(prec, p, r12);
   std::vector<int> cands;
-  for (int ns : ns_candidates(W)) {
-    HopParams q = p;
-    q.ns = ns;
-    if (hop_smem_bytes(prec, q, e.on) <= 200 * 1024) cands.push_back(ns);
+  if (tc) {
+    for (int ns = 1; ns <= 8; ns *= 2) {
+      HopParams q = p;
+      q.ns = ns;
+      if (hop_tc_smem_bytes(q) <= 200 * 1024) cands.push_back(ns);
+    }
+  } else {
+    for (int ns : ns_candidates(W)) {
+      HopParams q = p;
+      q.ns = ns;
+      if (hop_smem_bytes(prec, q, e.on) <= 200 * 1024) cands.push_back(ns);
+    }
   }
   if (cands.empty()) { g_last_error = "hop: shared memory"; return MDWF_ERR_ARG; }
-  const int dflt = std::min(ns_default(W), cands.back());
+  const int dflt = tc ? cands.back() : std::min(ns_default(W), cands.back());
   const std::string key = key_of(c, dag ? "hopdag" : "hop", prec, in.nrhs,
-                                 std::string(e.on ? "epi" : "plain") + chain_sig(e.post) + chain_sig(e.fin) +
-                                     (p.has_center ? "c" : "") + (p.axpy_r ? "a" : "") + (red.mode ? "r" : ""));
+                                 std::string(tc ? "tc" : "") + (e.on ? "epi" : "plain") + chain_sig(e.post) +
+                                     chain_sig(e.fin) + (p.has_center ? "c" : "") + (p.axpy_r ? "a" : "") +
+                                     (red.mode ? "r" : ""));
   auto run = [&](int ns) -> int {
     HopParams q = p;
     q.ns = ns;
@@ -406,7 +418,7 @@ int hop(mdwf_ctx* c, int prec, bool dag, const Field& in, const Field& out, int 
       CKS(ensure_reduce(c, blocks, in.nrhs));
       q.red.partials = c->partials;
     }
-    cudaError_t err = launch_hop(prec, dag, r12, e.on, q, st);
+    cudaError_t err = tc ? launch_hop_tc(prec, dag, true, q, st) : launch_hop(prec, dag, r12, e.on, q, st);
     c->launches++;
     c->bytes += half_bytes(in, prec) + gauge_bytes(c, prec) + (q.has_center ? half_bytes(e.center, prec) : 0.0) +
                 (q.axpy_r ? 2.0 * half_bytes(e.raxpy, prec) : half_bytes(out, prec));
@@ -483,6 +495,10 @@ int sl_convert(mdwf_ctx* c, int po, const Field& out, int pi, const Field& in, b
   return MDWF_SUCCESS;
 }
 
+// per-rhs Re <a, b> into host vector
+int dot(mdwf_ctx* c, int prec, const Field& a, const Field& b, std::vector<double>& out, cudaStream_t st);
+int rhs_axpy(mdwf_ctx* c, int prec, const Field& a, const Field& b, const std::vector<double>& coef, cudaStream_t st);
+
 Red red_store(mdwf_ctx* c, int nrhs) {
   Red r = red_none();
   r.mode = RED_STORE; r.counter = c->counter; r.out = c->red_out; r.nrhs = nrhs;
@@ -500,6 +516,39 @@ int norm2(mdwf_ctx* c, int prec, const Field& f, std::vector<double>& out, cudaS
   CK(cudaMemcpyAsync(c->red_host, c->red_out, f.nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   out.assign(c->red_host, c->red_host + f.nrhs);
+  return MDWF_SUCCESS;
+}
+
+int dot(mdwf_ctx* c, int prec, const Field& a, const Field& b, std::vector<double>& out, cudaStream_t st) {
+  SLParams p;
+  memset(&p, 0, sizeof p);
+  p.b = a; p.c = b; p.vh = c->vh; p.red = red_store(c, a.nrhs);
+  const int W = a.nrhs * a.Ls;
+  p.ns = ns_default(W);
+  CKS(ensure_reduce(c, (c->vh + p.ns - 1) / p.ns, a.nrhs));
+  p.red.partials = c->partials;
+  cudaError_t err = launch_dot(prec, p, st);
+  c->launches++;
+  c->bytes += 2.0 * half_bytes(a, prec);
+  if (err != cudaSuccess) { set_err("launch_dot", err); return MDWF_ERR_CUDA; }
+  CK(cudaMemcpyAsync(c->red_host, c->red_out, a.nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  out.assign(c->red_host, c->red_host + a.nrhs);
+  return MDWF_SUCCESS;
+}
+
+int rhs_axpy(mdwf_ctx* c, int prec, const Field& a, const Field& b, const std::vector<double>& coef, cudaStream_t st) {
+  for (size_t i = 0; i < coef.size(); i++) c->red_host[i] = coef[i];
+  CK(cudaMemcpyAsync(c->red_out, c->red_host, coef.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  SLParams p;
+  memset(&p, 0, sizeof p);
+  p.a = a; p.b = b; p.vh = c->vh; p.red = red_store(c, a.nrhs);
+  p.ns = ns_default(a.nrhs * a.Ls);
+  cudaError_t err = launch_rhs_axpy(prec, p, st);
+  c->launches++;
+  c->bytes += 3.0 * half_bytes(a, prec);
+  if (err != cudaSuccess) { set_err("launch_rhs_axpy", err); return MDWF_ERR_CUDA; }
+  CK(cudaStreamSynchronize(st));
   return MDWF_SUCCESS;
 }
 
@@ -702,13 +751,20 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
   const Ops o = ops_of(c, c->prm.mf);
   std::vector<double> tmp;
   CKS(norm2(c, F64, bt, S->bnorm2, st));
-  // r = M^+ b~ (FP64) ; p = r ; phat = D5 p
-  CKS(apply_mpc_dag(c, F64, bt, r64, st));
+  // r = M^+ b~ ; p = r ; phat = D5 p.  The inner (normal-equation) residual only needs
+  // the inner precision relative to itself, so the mixed solver forms it in FP32.
+  Field r32, res32;
   std::vector<double> g0;
-  CKS(norm2(c, F64, r64, g0, st));
   if (mixed) {
-    CKS(sl_convert(c, P, v.r, F64, r64, false, false, st));
+    CKS(ws_half(c, "r32", F32, nrhs, &r32));
+    CKS(ws_half(c, "res32", F32, nrhs, &res32));
+    CKS(sl_convert(c, F32, res32, F64, bt, false, false, st));
+    CKS(apply_mpc_dag(c, F32, res32, r32, st));
+    CKS(norm2(c, F32, r32, g0, st));
+    CKS(sl_convert(c, P, v.r, F32, r32, false, false, st));
   } else {
+    CKS(apply_mpc_dag(c, F64, bt, r64, st));
+    CKS(norm2(c, F64, r64, g0, st));
     CK(cudaMemcpyAsync(v.r.data, r64.data, field_bytes_of(r64, F64), cudaMemcpyDeviceToDevice, st));
   }
   CK(cudaMemcpyAsync(v.p.data, v.r.data, field_bytes_of(v.r, P), cudaMemcpyDeviceToDevice, st));
@@ -783,10 +839,16 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
       }
     }
     if (mixed) {
-      CKS(apply_mpc_dag(c, F64, res, r64, st));
-      std::vector<double> g;
-      CKS(norm2(c, F64, r64, g, st));
-      CKS(sl_convert(c, P, v.r, F64, r64, false, false, st));
+      // r = M^+ (b~ - M x) with the FP64 residual rounded to FP32 (relative precision of
+      // the inner iteration is all it needs), requantised to the inner storage
+      CKS(sl_convert(c, F32, res32, F64, res, false, false, st));
+      CKS(apply_mpc_dag(c, F32, res32, r32, st));
+      std::vector<double> g, rp;
+      CKS(norm2(c, F32, r32, g, st));
+      CKS(sl_convert(c, P, v.r, F32, r32, false, false, st));
+      // restore <r, p> = |r|^2 for the kept search direction: p += (|r|^2 - <r,p>)/|r|^2 r
+      CKS(dot(c, P, v.r, v.p, rp, st));
+      std::vector<double> coef(nrhs, 0.0);
       for (int r = 0; r < nrhs; r++) {
         CGScalars& s = c->cg_host[r];
         if (S->done[r]) { s.active = 0; continue; }
@@ -795,7 +857,10 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
         s.hit = 0;
         if (s.stop2 > 0.0 && g[r] <= s.stop2) s.stop2 = g[r] * 0.5;
         since_ru[r] = 0;
+        coef[r] = g[r] > 0.0 ? (g[r] - rp[r]) / g[r] : 0.0;
       }
+      CKS(rhs_axpy(c, P, v.p, v.r, coef, st));
+      CKS(sl_chain(c, P, v.ph, v.p, chain(o.D5(false)), 1.0, nullptr, 0.0, o.mf, st));
     }
     CKS(push_scalars(c, nrhs, st));
   }

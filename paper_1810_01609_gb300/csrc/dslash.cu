@@ -15,6 +15,7 @@
 // thread per (site, rhs, real component) applies the s-direction chains in place.
 #include "mdwf_impl.cuh"
 #include "mdwf_kernels.h"
+#include "mdwf_epi.cuh"
 
 namespace mdwf {
 
@@ -171,71 +172,16 @@ hop_kernel(const __grid_constant__ HopParams p) {
     const int ngrp = p.ns * nrhs;
     C* tileH = (C*)smem_raw;
     C* tileC = tileH + ngrp * 24 * LsP;
-    double* redsm = (double*)(tileC + (p.has_center ? ngrp * 24 * LsP : 0));
+    const size_t toff = ((size_t)ngrp * 24 * LsP * sizeof(C) * (p.has_center ? 2 : 1) + 15) & ~(size_t)15;
+    double* redsm = (double*)(smem_raw + toff);
     const int r = col / Ls, s = col - r * Ls;
     const int grp = site_l * nrhs + r;
-    const C mf = (C)p.mf;
     if (active) {
 #pragma unroll
       for (int k = 0; k < 24; k++) tileH[(grp * 24 + k) * LsP + s] = acc[k];
-      if (p.has_center) {
-        C v[24];
-        load_site<P>(p.center, x_cb, col, v);
-#pragma unroll
-        for (int k = 0; k < 24; k++) tileC[(grp * 24 + k) * LsP + s] = v[k];
-      }
     }
     __syncthreads();
-    const int nitems = ngrp * 24;
-    const C hc = (C)p.hc, cc = (C)p.cc;
-    for (int it = tid; it < nitems; it += blockDim.x) {
-      const int g = it / 24, comp = it - g * 24;
-      if ((long long)blockIdx.x * p.ns + g / nrhs >= p.g.vh) continue;
-      C* h = tileH + it * LsP;
-      chain_apply(p.post, comp, h, 1, Ls, mf);
-      if (p.has_center) {
-        C* cv = tileC + it * LsP;
-        chain_apply(p.cop, comp, cv, 1, Ls, mf);
-        for (int ss = 0; ss < Ls; ss++) h[ss] = cc * cv[ss] + hc * h[ss];
-      } else if (p.hc != 1.0) {
-        for (int ss = 0; ss < Ls; ss++) h[ss] = hc * h[ss];
-      }
-    }
-    __syncthreads();
-    double part = 0.0;
-    if (p.norm_pre && active) {
-      C n = 0;
-#pragma unroll
-      for (int k = 0; k < 24; k++) { C v = tileH[(grp * 24 + k) * LsP + s]; n += v * v; }
-      part = (double)n;
-    }
-    if (p.fin.op[0].kind != SOP_NONE) {
-      __syncthreads();
-      for (int it = tid; it < nitems; it += blockDim.x) {
-        const int g = it / 24, comp = it - g * 24;
-        if ((long long)blockIdx.x * p.ns + g / nrhs >= p.g.vh) continue;
-        chain_apply(p.fin, comp, tileH + it * LsP, 1, Ls, mf);
-      }
-      __syncthreads();
-    }
-    if (active) {
-      C v[24];
-#pragma unroll
-      for (int k = 0; k < 24; k++) v[k] = tileH[(grp * 24 + k) * LsP + s];
-      if (p.axpy_r) {
-        C rv[24];
-        load_site<P>(p.raxpy, x_cb, col, rv);
-        const C a = (C)p.red.cg[r].alpha;
-        C n = 0;
-#pragma unroll
-        for (int k = 0; k < 24; k++) { rv[k] -= a * v[k]; n += rv[k] * rv[k]; }
-        store_site<P>(p.raxpy, x_cb, col, rv);
-        part = (double)n;
-      } else {
-        store_site<P>(p.out, x_cb, col, v);
-      }
-    }
-    if (p.red.mode != RED_NONE) block_grid_reduce(p.red, part, redsm, Ls, p.ns);
+    hop_epilogue<P>(p, tileH, tileC, redsm, p.ns);
   }
 }
 
@@ -266,11 +212,8 @@ static cudaError_t launch_p(const HopParams& p, bool dag, bool r12, bool epi, in
 
 size_t hop_smem_bytes(int prec, const HopParams& p, bool epi) {
   if (!epi) return 0;
-  const size_t csz = prec == F64 ? 8 : 4;
-  const size_t ngrp = (size_t)p.ns * p.in.nrhs;
-  const size_t tile = ngrp * 24 * (p.in.Ls + 1) * csz;
-  const size_t threads = (size_t)p.ns * p.in.nrhs * p.in.Ls;
-  return tile * (p.has_center ? 2 : 1) + 2 * threads * sizeof(double) + 16;
+  const int threads = p.ns * p.in.nrhs * p.in.Ls;
+  return epi_smem_bytes(prec == F64 ? 8 : 4, p.ns, p.in.nrhs, p.in.Ls, p.has_center, threads);
 }
 
 cudaError_t launch_hop(int prec, bool dag, bool r12, bool epi, const HopParams& p, cudaStream_t st) {

@@ -271,27 +271,27 @@ struct Red {
   int nrhs;
 };
 
-// Sum per-thread values (each belonging to rhs index r) over the block, then over the
-// grid.  vals: smem scratch of blockDim.x doubles; the block's threads are laid out as
-// (site_l, r, s) with s fastest, i.e. tid = (site_l * nrhs + r) * Ls + s.
-__device__ inline void block_grid_reduce(const Red& red, double v, double* sm, int Ls, int ns) {
+// Grid reduction of per-5D-site values sm[(site_l * nrhs + r) * Ls + s], i < ns * nrhs * Ls,
+// already in shared memory (scratch must hold max(ns*nrhs*Ls, blockDim.x) + ns*nrhs doubles):
+// fixed-order sums per (site, rhs), per rhs over the block, then the last block to finish
+// sums the block partials in a fixed order and runs the scalar program.
+__device__ inline void block_grid_reduce_sm(const Red& red, double* sm, int Ls, int ns) {
   const int tid = threadIdx.x;
   const int nrhs = red.nrhs;
-  sm[tid] = v;
-  __syncthreads();
-  // stage 1: one thread per (site_l, r) sums its Ls values
   const int ngrp = ns * nrhs;
-  double* sm2 = sm + blockDim.x;
-  if (tid < ngrp) {
+  const int nitems = ngrp * Ls;
+  double* sm2 = sm + (nitems > (int)blockDim.x ? nitems : (int)blockDim.x);
+  __syncthreads();
+  for (int gi = tid; gi < ngrp; gi += blockDim.x) {
     double acc = 0.0;
-    for (int s = 0; s < Ls; s++) acc += sm[tid * Ls + s];
-    sm2[tid] = acc;
+    for (int s = 0; s < Ls; s++) acc += sm[gi * Ls + s];
+    sm2[gi] = acc;
   }
   __syncthreads();
-  if (tid < nrhs) {
+  for (int r = tid; r < nrhs; r += blockDim.x) {
     double acc = 0.0;
-    for (int i = 0; i < ns; i++) acc += sm2[i * nrhs + tid];
-    red.partials[(long long)blockIdx.x * nrhs + tid] = acc;
+    for (int i = 0; i < ns; i++) acc += sm2[i * nrhs + r];
+    red.partials[(long long)blockIdx.x * nrhs + r] = acc;
   }
   __shared__ unsigned int ticket;
   __threadfence();
@@ -341,6 +341,12 @@ __device__ inline void block_grid_reduce(const Red& red, double v, double* sm, i
     __syncthreads();
   }
   if (tid == 0) *red.counter = 0u;
+}
+
+// Per-thread value version for kernels whose threads are exactly the (site_l, r, s) sites.
+__device__ inline void block_grid_reduce(const Red& red, double v, double* sm, int Ls, int ns) {
+  sm[threadIdx.x] = v;
+  block_grid_reduce_sm(red, sm, Ls, ns);
 }
 
 }  // namespace mdwf

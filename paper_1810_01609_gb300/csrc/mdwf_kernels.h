@@ -34,6 +34,7 @@ cudaError_t launch_hop(int prec, bool dag, bool r12, bool epi, const HopParams& 
 
 // tensor-core hop for F16/BF16 (returns cudaErrorNotSupported when the shape is not covered)
 bool hop_tc_supported(int prec, const HopParams& p, bool r12);
+size_t hop_tc_smem_bytes(const HopParams& p);   // p.ns = warps (4D sites) per CTA
 cudaError_t launch_hop_tc(int prec, bool dag, bool epi, const HopParams& p, cudaStream_t st);
 
 // ---------------------------------------------------------------- s-local kernels (slocal.cu)
@@ -54,6 +55,10 @@ cudaError_t launch_chain(int prec, const SLParams& p, cudaStream_t st);
 cudaError_t launch_axpby(int prec, const SLParams& p, cudaStream_t st);
 // x += alpha p ; p = r + beta p ; phat = chain(p)   (a = p, b = r, c = phat; x separate)
 cudaError_t launch_cg_update(int prec_x, int prec, const SLParams& p, cudaStream_t st);
+// Re <b, c> per rhs into red.out (RED_STORE)
+cudaError_t launch_dot(int prec, const SLParams& p, cudaStream_t st);
+// a[rhs] += red.out[rhs] * b[rhs]
+cudaError_t launch_rhs_axpy(int prec, const SLParams& p, cudaStream_t st);
 // a(prec_out) (+)= b(prec_in); ca = 1 accumulate, 0 overwrite; cb != 0: zero b afterwards
 cudaError_t launch_convert(int prec_out, int prec_in, const SLParams& p, cudaStream_t st);
 

@@ -156,6 +156,44 @@ __global__ void __launch_bounds__(MAXTHREADS) convert_kernel(const __grid_consta
   }
 }
 
+// Re <b, c> per right-hand side (FP64 accumulated)
+template <int P>
+__global__ void __launch_bounds__(MAXTHREADS) dot_kernel(const __grid_constant__ SLParams p) {
+  using C = typename PT<P>::C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Ls = p.b.Ls, nrhs = p.b.nrhs, W = Ls * nrhs;
+  const int tid = threadIdx.x, site_l = tid / W, col = tid - site_l * W;
+  const long long x_cb = (long long)blockIdx.x * p.ns + site_l;
+  double part = 0.0;
+  if (x_cb < p.vh) {
+    C u[24], v[24];
+    load_site<P>(p.b, x_cb, col, u);
+    load_site<P>(p.c, x_cb, col, v);
+    C n = 0;
+#pragma unroll
+    for (int k = 0; k < 24; k++) n += u[k] * v[k];
+    part = (double)n;
+  }
+  block_grid_reduce(p.red, part, (double*)smem_raw, Ls, p.ns);
+}
+
+// a[rhs] += coef[rhs] * b[rhs], coef read from device memory (p.red.out)
+template <int P>
+__global__ void __launch_bounds__(MAXTHREADS) rhs_axpy_kernel(const __grid_constant__ SLParams p) {
+  using C = typename PT<P>::C;
+  const int Ls = p.b.Ls, nrhs = p.b.nrhs, W = Ls * nrhs;
+  const int tid = threadIdx.x, site_l = tid / W, col = tid - site_l * W;
+  const long long x_cb = (long long)blockIdx.x * p.ns + site_l;
+  if (x_cb >= p.vh) return;
+  const C cf = (C)p.red.out[col / Ls];
+  C u[24], v[24];
+  load_site<P>(p.a, x_cb, col, u);
+  load_site<P>(p.b, x_cb, col, v);
+#pragma unroll
+  for (int k = 0; k < 24; k++) u[k] += cf * v[k];
+  store_site<P>(p.a, x_cb, col, u);
+}
+
 template <typename K>
 static cudaError_t go(K kern, const SLParams& p, int W, size_t smem, cudaStream_t st) {
   static_assert(sizeof(SLParams) < 4000, "param size");
@@ -210,11 +248,34 @@ cudaError_t launch_cg_update(int prec_x, int prec, const SLParams& p, cudaStream
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_dot(int prec, const SLParams& p, cudaStream_t st) {
+  const int W = p.b.nrhs * p.b.Ls;
+  const size_t smem = 2 * (size_t)p.ns * W * sizeof(double) + 16;
+  switch (prec) {
+    case F64: return go(dot_kernel<F64>, p, W, smem, st);
+    case F32: return go(dot_kernel<F32>, p, W, smem, st);
+    case F16: return go(dot_kernel<F16>, p, W, smem, st);
+    case BF16: return go(dot_kernel<BF16>, p, W, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_rhs_axpy(int prec, const SLParams& p, cudaStream_t st) {
+  const int W = p.b.nrhs * p.b.Ls;
+  switch (prec) {
+    case F64: return go(rhs_axpy_kernel<F64>, p, W, 0, st);
+    case F32: return go(rhs_axpy_kernel<F32>, p, W, 0, st);
+    case F16: return go(rhs_axpy_kernel<F16>, p, W, 0, st);
+    case BF16: return go(rhs_axpy_kernel<BF16>, p, W, 0, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_convert(int po, int pi, const SLParams& p, cudaStream_t st) {
   const int W = p.b.nrhs * p.b.Ls;
 #define CV(A, B) if (po == A && pi == B) return go(convert_kernel<A, B>, p, W, 0, st);
   CV(F64, F64) CV(F64, F32) CV(F64, F16) CV(F64, BF16)
-  CV(F32, F64) CV(F16, F64) CV(BF16, F64) CV(F32, F32)
+  CV(F32, F64) CV(F16, F64) CV(BF16, F64) CV(F32, F32) CV(F16, F32) CV(BF16, F32)
 #undef CV
   return cudaErrorInvalidValue;
 }

@@ -107,6 +107,20 @@ def test_apply_parity(case, prec, monkeypatch):
         assert err <= TOL[prec], (op, prec, err)
 
 
+@pytest.mark.parametrize("prec", ["f16", "bf16"])
+def test_tensor_core_hop_matches_oracle(prec, monkeypatch):
+    """The mma.sync hop kernel (MDWF_TC=1) on every hop-based op, several tiles + ragged."""
+    monkeypatch.setenv("MDWF_TC", "1")
+    for case in CASES:
+        dims, Ls, nrhs = case
+        m, ctx, U, Ub, psi, p = _setup(dims, Ls, nrhs)
+        par = parity_of(dims)
+        for op in ["HOP_EO", "HOP_OE_DAG", "HOP_OE_M5INV", "MPC", "MPC_DAG", "FULL_D"]:
+            got = _gpu_apply(m, ctx, op, prec, psi, nrhs)
+            ref = np.stack([_oracle(op, Ub, psi[r], p, par) for r in range(nrhs)])
+            assert rel(got, ref) <= TOL[prec], (op, prec, case)
+
+
 def test_recon12_matches_recon18():
     m = lib()
     dims, Ls = (4, 4, 4, 4), 6
