@@ -204,6 +204,23 @@ int mdwf_fh_source(mdwf_ctx* ctx, const double* q4d, double* out4d, int nrhs, in
 int mdwf_contract_nucleon(mdwf_ctx* ctx, const double* u1, const double* d,
                           const double* u2, double* corr, int where, void* stream);
 
+/* Allocation-free nucleon contraction (the paper has no counterpart; it serves callers
+ * that cannot allocate device memory: code running during CUDA graph capture, programs
+ * whose device memory belongs to a pool allocator that forbids other allocations, hosts
+ * that plan every byte of device memory up front).  Computes exactly what
+ * mdwf_contract_nucleon computes, for DEVICE pointers only (u1, d, u2: 12-column 4D
+ * propagators; corr: T complex values), without any cudaMalloc or cudaFree: the per-site
+ * scratch lives in a fixed 8 MiB array inside the library, which every GPU that loads the
+ * library keeps until the process exits.  Lattices with more than 524288 4D sites are
+ * rejected with MDWF_ERR_ARG (use mdwf_contract_nucleon).  The first call on each device
+ * looks up the array's device address with that device current; make that first call
+ * before any stream capture.  All calls share the array: calls whose kernels overlap on
+ * the GPU (different streams, or the same call issued from several threads) race and
+ * must be serialised by the caller.  Detail of a failure: mdwf_noalloc_last_error(). */
+int mdwf_contract_nucleon_noalloc(const mdwf_ctx* ctx, const double* u1, const double* d,
+                                  const double* u2, double* corr, void* stream);
+const char* mdwf_noalloc_last_error(void);
+
 /* Autotuner control: enable (1) / disable (0) brute-force launch tuning (default from
  * env MDWF_TUNE, on).  The cache is a std::map keyed by kernel, lattice, Ls, nrhs,
  * precision and mode; MDWF_TUNE_CACHE names a JSON file it is loaded from and saved to. */

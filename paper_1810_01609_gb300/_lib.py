@@ -73,6 +73,8 @@ _SIGS = {
     "mdwf_project_4d": (_I, [_V, _V, _V, _I, _I, _V]),
     "mdwf_fh_source": (_I, [_V, _V, _V, _I, _I, _V]),
     "mdwf_contract_nucleon": (_I, [_V, _V, _V, _V, _V, _I, _V]),
+    "mdwf_contract_nucleon_noalloc": (_I, [_V, _V, _V, _V, _V, _V]),
+    "mdwf_noalloc_last_error": (ctypes.c_char_p, []),
     "mdwf_set_tuning": (_I, [_V, _I]),
     "mdwf_tune_entries": (_I, [_V, ctypes.POINTER(_I)]),
     "mdwf_tune_entry": (_I, [_V, _I, ctypes.c_char_p, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
@@ -215,6 +217,17 @@ def mdwf_contract_nucleon(ctx, u1, d, u2, corr, stream=None):
         raise ValueError("all arrays must be host or all device")
     return _check(load().mdwf_contract_nucleon(ctx, ps[0][0], ps[1][0], ps[2][0], ps[3][0], wheres.pop(),
                                                _stream(stream)))
+
+
+def mdwf_contract_nucleon_noalloc(ctx, u1, d, u2, corr, stream=None):
+    """Allocation-free contraction (device arrays only); see include/mdwf.h."""
+    ps = [ptr(x) for x in (u1, d, u2, corr)]
+    if any(w != MDWF_DEVICE for _, w in ps):
+        raise ValueError("mdwf_contract_nucleon_noalloc takes device arrays only")
+    code = load().mdwf_contract_nucleon_noalloc(ctx, ps[0][0], ps[1][0], ps[2][0], ps[3][0], _stream(stream))
+    if code != MDWF_SUCCESS:
+        raise MdwfError(code, load().mdwf_noalloc_last_error().decode())
+    return code
 
 
 def mdwf_set_tuning(ctx, enable):

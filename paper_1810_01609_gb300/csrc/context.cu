@@ -1357,3 +1357,30 @@ long long mdwf_launch_count(const mdwf_ctx* c) { return c ? c->launches : 0; }
 double mdwf_algorithmic_bytes(const mdwf_ctx* c) { return c ? c->bytes : 0.0; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- internal accessors
+// (used by translation units that must not touch the context's allocations)
+namespace mdwf {
+
+bool ctx_geom(const mdwf_ctx* c, Geom* g) {
+  if (!c || !g) return false;
+  *g = c->g;
+  return true;
+}
+
+// Spin matrices of the nucleon contraction in the library's chiral basis.
+void nucleon_mats(NucMats* m) {
+  const M4 g5 = mmul(mmul(gamma_mu(0), gamma_mu(1)), mmul(gamma_mu(2), gamma_mu(3)));
+  const M4 cg5 = mmul(mmul(gamma_mu(1), gamma_mu(3)), g5);
+  const M4 cg5b = mmul(mmul(gamma_mu(3), mdag(cg5)), gamma_mu(3));
+  const M4 g4 = gamma_mu(3);
+  for (int i = 0; i < 4; i++)
+    for (int j = 0; j < 4; j++) {
+      m->car[i * 4 + j] = cg5.m[i][j].real(); m->cai[i * 4 + j] = cg5.m[i][j].imag();
+      m->cbr[i * 4 + j] = cg5b.m[i][j].real(); m->cbi[i * 4 + j] = cg5b.m[i][j].imag();
+      const cd pv = 0.5 * ((i == j ? 1.0 : 0.0) + g4.m[i][j]);
+      m->pr[i * 4 + j] = pv.real(); m->pi[i * 4 + j] = pv.imag();
+    }
+}
+
+}  // namespace mdwf
