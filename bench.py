@@ -163,10 +163,16 @@ def kernel_only(args, m, ctx, dims, Ls, seed, stream):
     fout = torch.zeros(nb, dtype=torch.uint8, device="cuda")
     src = torch.from_numpy(inputs.gaussian_spinor5d(dims, Ls, seed + 100)).cuda()
     m.mdwf_pack(ctx.h, src, fin, prec, 1, stream)
+    m.mdwf_apply(ctx.h, m.OP[args.op], prec, fin, fout, 1, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
     for _ in range(args.kernel_launches):
         m.mdwf_apply(ctx.h, m.OP[args.op], prec, fin, fout, 1, stream)
+    e1.record(stream)
     torch.cuda.synchronize()
-    print(json.dumps({"kernel_only": args.op, "launches": args.kernel_launches, "tune": ctx.tune_entries()}))
+    ms = e0.elapsed_time(e1) / max(1, args.kernel_launches)
+    print(json.dumps({"kernel_only": args.op, "launches": args.kernel_launches, "ms_per_launch": ms,
+                      "tune": ctx.tune_entries()}))
 
 
 def main():

@@ -392,10 +392,10 @@ int hop(mdwf_ctx* c, int prec, bool dag, const Field& in, const Field& out, int 
   const bool tc = (use_tc && use_tc[0] == '1') && hop_tc_supported(prec, p, r12);
   std::vector<int> cands;
   if (tc) {
-    for (int ns = 1; ns <= 8; ns *= 2) {
+    for (int ns = 1; ns <= 32; ns *= 2) {
       HopParams q = p;
       q.ns = ns;
-      if (hop_tc_smem_bytes(q) <= 200 * 1024) cands.push_back(ns);
+      if ((ns == 1 || ns * W <= 256) && hop_tc_smem_bytes(q) <= 200 * 1024) cands.push_back(ns);
     }
   } else {
     for (int ns : ns_candidates(W)) {
@@ -405,7 +405,7 @@ int hop(mdwf_ctx* c, int prec, bool dag, const Field& in, const Field& out, int 
     }
   }
   if (cands.empty()) { g_last_error = "hop: shared memory"; return MDWF_ERR_ARG; }
-  const int dflt = tc ? cands.back() : std::min(ns_default(W), cands.back());
+  const int dflt = std::min(ns_default(W), cands.back());
   const std::string key = key_of(c, dag ? "hopdag" : "hop", prec, in.nrhs,
                                  std::string(tc ? "tc" : "") + (e.on ? "epi" : "plain") + chain_sig(e.post) +
                                      chain_sig(e.fin) + (p.has_center ? "c" : "") + (p.axpy_r ? "a" : "") +

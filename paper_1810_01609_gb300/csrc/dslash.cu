@@ -16,6 +16,7 @@
 #include "mdwf_impl.cuh"
 #include "mdwf_kernels.h"
 #include "mdwf_epi.cuh"
+#include <type_traits>
 
 namespace mdwf {
 
@@ -125,6 +126,118 @@ __device__ __forceinline__ void load_link(const void* base, long long off, typen
   }
 }
 
+// SU(3) on a projected half spinor h (2 slots x 3 colours, complex) and reconstruction:
+// upper spins += U h, lower spins += -sig X_mu^+ U h.
+template <int MU, int SIG, typename C>
+__device__ __forceinline__ void su3_recon(const C h[12], const C* U, C acc[24]) {
+  const C sg = (C)SIG;
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    cplx<C> u0, u1;
+    {
+      const C ur = U[6 * a], ui = U[6 * a + 1];
+      u0.re = ur * h[0] - ui * h[1]; u0.im = ur * h[1] + ui * h[0];
+      u1.re = ur * h[6] - ui * h[7]; u1.im = ur * h[7] + ui * h[6];
+    }
+#pragma unroll
+    for (int b = 1; b < 3; b++) {
+      const C ur = U[2 * (3 * a + b)], ui = U[2 * (3 * a + b) + 1];
+      u0.re += ur * h[2 * b] - ui * h[2 * b + 1];
+      u0.im += ur * h[2 * b + 1] + ui * h[2 * b];
+      u1.re += ur * h[6 + 2 * b] - ui * h[6 + 2 * b + 1];
+      u1.im += ur * h[6 + 2 * b + 1] + ui * h[6 + 2 * b];
+    }
+    ARE(0, a) += u0.re; AIM(0, a) += u0.im;
+    ARE(1, a) += u1.re; AIM(1, a) += u1.im;
+    if (MU == 0) {         // lower0 = s i Uh1 ; lower1 = s i Uh0
+      ARE(2, a) -= sg * u1.im; AIM(2, a) += sg * u1.re;
+      ARE(3, a) -= sg * u0.im; AIM(3, a) += sg * u0.re;
+    } else if (MU == 1) {  // lower0 = s Uh1 ; lower1 = -s Uh0
+      ARE(2, a) += sg * u1.re; AIM(2, a) += sg * u1.im;
+      ARE(3, a) -= sg * u0.re; AIM(3, a) -= sg * u0.im;
+    } else if (MU == 2) {  // lower0 = s i Uh0 ; lower1 = -s i Uh1
+      ARE(2, a) -= sg * u0.im; AIM(2, a) += sg * u0.re;
+      ARE(3, a) += sg * u1.im; AIM(3, a) -= sg * u1.re;
+    } else {               // lower0 = -s Uh0 ; lower1 = -s Uh1
+      ARE(2, a) -= sg * u0.re; AIM(2, a) -= sg * u0.im;
+      ARE(3, a) -= sg * u1.re; AIM(3, a) -= sg * u1.im;
+    }
+  }
+}
+
+template <int P>
+__device__ __forceinline__ auto mk2(float a, float b) {
+  if constexpr (P == F16) return __floats2half2_rn(a, b);
+  else return __floats2bfloat162_rn(a, b);
+}
+
+// Neighbour column -> projected half spinor h (slot j, colour c at h[6j + 2c]) in the
+// compute precision.  F16 / BF16 project in 16-bit pairs before converting (one rounding
+// of the pair sum, then exact conversion), then scale by the per-site norm.
+template <int P, int MU, int SIG>
+__device__ __forceinline__ void load_proj(const Field& f, unsigned nbr, int col, typename PT<P>::C h[12]) {
+  using C = typename PT<P>::C;
+  if constexpr (P == F64 || P == F32) {
+    C psi[24];
+    load_site<P>(f, nbr, col, psi);
+    const C sg = (C)SIG;
+#pragma unroll
+    for (int co = 0; co < 3; co++) {
+      C* h0 = h + 2 * co;
+      C* h1 = h + 6 + 2 * co;
+      if (MU == 0) {
+        h0[0] = PRE(0, co) + sg * PIM(3, co); h0[1] = PIM(0, co) - sg * PRE(3, co);
+        h1[0] = PRE(1, co) + sg * PIM(2, co); h1[1] = PIM(1, co) - sg * PRE(2, co);
+      } else if (MU == 1) {
+        h0[0] = PRE(0, co) - sg * PRE(3, co); h0[1] = PIM(0, co) - sg * PIM(3, co);
+        h1[0] = PRE(1, co) + sg * PRE(2, co); h1[1] = PIM(1, co) + sg * PIM(2, co);
+      } else if (MU == 2) {
+        h0[0] = PRE(0, co) + sg * PIM(2, co); h0[1] = PIM(0, co) - sg * PRE(2, co);
+        h1[0] = PRE(1, co) - sg * PIM(3, co); h1[1] = PIM(1, co) + sg * PRE(3, co);
+      } else {
+        h0[0] = PRE(0, co) - sg * PRE(2, co); h0[1] = PIM(0, co) - sg * PIM(2, co);
+        h1[0] = PRE(1, co) - sg * PRE(3, co); h1[1] = PIM(1, co) - sg * PIM(3, co);
+      }
+    }
+  } else {
+    using H2 = typename std::conditional<P == F16, __half2, __nv_bfloat162>::type;
+    const uint4* d = (const uint4*)f.data;
+    const unsigned W = (unsigned)f.W();
+    float nrm = 1.0f;
+    if constexpr (P == F16) nrm = __ldg(f.norm + nbr * W + col);
+    const H2 ps = mk2<P>((float)SIG, (float)SIG);
+#pragma unroll
+    for (int co = 0; co < 3; co++) {
+      const uint4 q = __ldg(d + (nbr * 3 + co) * W + col);
+      const H2 w0 = *(const H2*)&q.x, w1 = *(const H2*)&q.y, w2 = *(const H2*)&q.z, w3 = *(const H2*)&q.w;
+      H2 r0, r1;
+      if (MU == 0 || MU == 2) {
+        // i * w = (-w.im, w.re): h0 = w0 - s i wA, h1 = w1 -+ s i wB
+        const H2 iA = MU == 0 ? __lowhigh2highlow(w3) : __lowhigh2highlow(w2);
+        const H2 iB = MU == 0 ? __lowhigh2highlow(w2) : __lowhigh2highlow(w3);
+        // -s i wA = s (wA.im, -wA.re) = iA * (s, -s)
+        const H2 m0 = mk2<P>((float)SIG, (float)-SIG);
+        r0 = __hfma2(iA, m0, w0);
+        r1 = MU == 0 ? __hfma2(iB, m0, w1) : __hfma2(iB, __hneg2(m0), w1);
+      } else if (MU == 1) {
+        r0 = __hfma2(w3, __hneg2(ps), w0);
+        r1 = __hfma2(w2, ps, w1);
+      } else {
+        r0 = __hfma2(w2, __hneg2(ps), w0);
+        r1 = __hfma2(w3, __hneg2(ps), w1);
+      }
+      float2 f0, f1;
+      if constexpr (P == F16) { f0 = __half22float2(r0); f1 = __half22float2(r1); }
+      else { f0 = __bfloat1622float2(r0); f1 = __bfloat1622float2(r1); }
+      h[2 * co] = f0.x * nrm; h[2 * co + 1] = f0.y * nrm;
+      h[6 + 2 * co] = f1.x * nrm; h[6 + 2 * co + 1] = f1.y * nrm;
+    }
+  }
+}
+
+// Link staging stride in shared memory (compute-precision reals per link, 16-byte rows)
+template <typename C> __host__ __device__ constexpr int link_stride() { return sizeof(C) == 8 ? 18 : 20; }
+
 template <int P, bool DAG, bool R12, bool EPI>
 __global__ void __launch_bounds__(MAXTHREADS)
 hop_kernel(const __grid_constant__ HopParams p) {
@@ -132,53 +245,72 @@ hop_kernel(const __grid_constant__ HopParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Ls = p.in.Ls, nrhs = p.in.nrhs;
   const int W = Ls * nrhs;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
   const int site_l = tid / W;
   const int col = tid - site_l * W;
-  const long long x_cb = (long long)blockIdx.x * p.ns + site_l;
+  const long long site0 = (long long)blockIdx.x * p.ns;
+  const long long x_cb = site0 + site_l;
   const bool active = x_cb < p.g.vh;
   constexpr int SF = DAG ? -1 : 1;
+  constexpr int LSTR = link_stride<C>();
+  // shared: links of the CTA's sites (compute precision), neighbour table, epilogue
+  C* slink = (C*)smem_raw;
+  unsigned* snbr = (unsigned*)(slink + p.ns * 8 * LSTR);
+  unsigned char* epi_base = (unsigned char*)(snbr + ((p.ns * 8 + 3) & ~3));
+
+  // phase 0: one thread per (site, direction) loads and converts the link, and finds the
+  // neighbour; forward links carry the boundary phase on t at T-1, backward ones on t at 0
+  for (int i = tid; i < p.ns * 8; i += nt) {
+    const long long x = site0 + (i >> 3);
+    if (x >= p.g.vh) continue;
+    const int d = i & 7, mu = d & 3;
+    int c[4];
+    cb_coords(p.g, x, p.pout, c);
+    snbr[i] = (unsigned)nbr_cb(p.g, c, mu, d < 4 ? +1 : -1);
+    C U[18];
+    const bool flip = R12 && mu == 3 && p.t_bc < 0 && (d < 4 ? c[3] == p.g.T - 1 : c[3] == 0);
+    load_link<P, R12>(p.gauge, (x * 8 + d) * p.gs, U, flip);
+#pragma unroll
+    for (int k = 0; k < 18; k++) slink[i * LSTR + k] = U[k];
+  }
+  __syncthreads();
 
   C acc[24];
 #pragma unroll
   for (int i = 0; i < 24; i++) acc[i] = 0;
-
   if (active) {
-    int c[4];
-    cb_coords(p.g, x_cb, p.pout, c);
-    const long long gbase = x_cb * 8 * p.gs;
-    C U[18], psi[24];
-    // forward links carry the boundary phase on t at T-1, backward ones on t at 0
-#define HOP_MU(MU)                                                                   \
-    {                                                                                \
-      load_site<P>(p.in, nbr_cb(p.g, c, MU, +1), col, psi);                          \
-      load_link<P, R12>(p.gauge, gbase + (MU) * p.gs, U,                             \
-                        R12 && MU == 3 && c[3] == p.g.T - 1 && p.t_bc < 0);          \
-      hop_dir<MU, SF>(psi, U, acc);                                                  \
-      load_site<P>(p.in, nbr_cb(p.g, c, MU, -1), col, psi);                          \
-      load_link<P, R12>(p.gauge, gbase + (4 + MU) * p.gs, U,                         \
-                        R12 && MU == 3 && c[3] == 0 && p.t_bc < 0);                  \
-      hop_dir<MU, -SF>(psi, U, acc);                                                 \
-    }
-    HOP_MU(0) HOP_MU(1) HOP_MU(2) HOP_MU(3)
-#undef HOP_MU
+    const unsigned* nb = snbr + site_l * 8;
+    const C* lk = slink + site_l * 8 * LSTR;
+    C h[12];
+#define HOP_D(D, MU, SIG)                                   \
+    load_proj<P, MU, SIG>(p.in, nb[D], col, h);             \
+    su3_recon<MU, SIG>(h, lk + (D) * LSTR, acc);
+    HOP_D(0, 0, SF) HOP_D(4, 0, -SF) HOP_D(1, 1, SF) HOP_D(5, 1, -SF)
+    HOP_D(2, 2, SF) HOP_D(6, 2, -SF) HOP_D(3, 3, SF) HOP_D(7, 3, -SF)
+#undef HOP_D
   }
 
   if constexpr (!EPI) {
     if (active) store_site<P>(p.out, x_cb, col, acc);
     return;
   } else {
-    const int LsP = Ls + 1;
+    const int GS = tile_gstr(Ls);
     const int ngrp = p.ns * nrhs;
-    C* tileH = (C*)smem_raw;
-    C* tileC = tileH + ngrp * 24 * LsP;
-    const size_t toff = ((size_t)ngrp * 24 * LsP * sizeof(C) * (p.has_center ? 2 : 1) + 15) & ~(size_t)15;
-    double* redsm = (double*)(smem_raw + toff);
+    C* tileH = (C*)epi_base;
+    C* tileC = tileH + ngrp * GS;
+    const size_t toff = ((size_t)ngrp * GS * sizeof(C) * (p.has_center ? 2 : 1) + 15) & ~(size_t)15;
+    double* redsm = (double*)(epi_base + toff);
     const int r = col / Ls, s = col - r * Ls;
     const int grp = site_l * nrhs + r;
     if (active) {
+      C* dst = tileH + grp * GS + s * TSTR;
+      if constexpr (sizeof(C) == 4) {
 #pragma unroll
-      for (int k = 0; k < 24; k++) tileH[(grp * 24 + k) * LsP + s] = acc[k];
+        for (int k = 0; k < 24; k += 4) *(float4*)(dst + k) = make_float4(acc[k], acc[k + 1], acc[k + 2], acc[k + 3]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 24; k += 2) *(double2*)(dst + k) = make_double2(acc[k], acc[k + 1]);
+      }
     }
     __syncthreads();
     hop_epilogue<P>(p, tileH, tileC, redsm, p.ns);
@@ -211,9 +343,13 @@ static cudaError_t launch_p(const HopParams& p, bool dag, bool r12, bool epi, in
 }
 
 size_t hop_smem_bytes(int prec, const HopParams& p, bool epi) {
-  if (!epi) return 0;
+  const size_t csz = prec == F64 ? 8 : 4;
+  const size_t links = (size_t)p.ns * 8 * (prec == F64 ? 18 : 20) * csz;
+  const size_t nbr = (size_t)((p.ns * 8 + 3) & ~3) * 4;
+  const size_t pre = (links + nbr + 15) & ~(size_t)15;
+  if (!epi) return pre;
   const int threads = p.ns * p.in.nrhs * p.in.Ls;
-  return epi_smem_bytes(prec == F64 ? 8 : 4, p.ns, p.in.nrhs, p.in.Ls, p.has_center, threads);
+  return pre + epi_smem_bytes(csz, p.ns, p.in.nrhs, p.in.Ls, p.has_center, threads);
 }
 
 cudaError_t launch_hop(int prec, bool dag, bool r12, bool epi, const HopParams& p, cudaStream_t st) {

@@ -1,26 +1,21 @@
 // Tensor-core Wilson hop for half-precision storage (F16 + per-site norm, BF16), fused
-// with the s-direction epilogue of mdwf_epi.cuh.  The SU(3) products of the stencil
-// (Sec. "Current State of the Art": a radius-one stencil with small dense blocks) run as
-// warp-level mma.sync.m16n8k8 (f16/bf16 inputs, FP32 accumulation) on sm_103a.
+// with the s-direction epilogue of mdwf_epi.cuh (Sec. "Current State of the Art": a
+// radius-one stencil with small dense diagonal blocks).  sm_103a warp-level
+// mma.sync.m16n8k16 with FP32 accumulation carries the SU(3) products.
 //
-// Mapping.  One warp owns one 4D site x and loops over its W = nrhs * Ls columns (5D
-// sites) in tiles of 8.  For direction d (mu = d & 3, forward for d < 4), with
-// sig = +1 for (1 - gamma_mu) and -1 for (1 + gamma_mu):
-//   rows (16)  = (column c in the tile, slot j in {0,1}); slot j holds the half spinor
-//                h_j = psi_j - sig (X_mu psi_d)_j of the neighbour column, which is
-//                psi_j + kappa * psi_{partner(j)} with kappa in {+-1, +-i}, formed in
-//                f16x2 straight from the stored chunk (one 16-byte load = one colour,
-//                4 spins) without conversion;
-//   K (8)      = input colour (re, im), 3 used;
-//   N (8)      = output colour (re, im), 3 used;
-//   B          = U_d embedded as a real 6x6 matrix, built once per site per direction.
-// The MMA result (U_d h)_j is scaled in FP32 by the neighbour's per-site norm (rows
-// differ per column) and accumulated: upper spin j += it, and lower spin
-// (j or 1-j, by mu) += zeta * it with zeta = -sig X_mu^+ entry in {+-1, +-i}; the two
-// lower contributions of a column are joined with one shuffle at the end of the tile.
-// Every multiply of two stored values is exact in FP32 and sums are FP32, so the
-// arithmetic matches an FP32 evaluation of the half-precision inputs up to the rounding
-// of the f16x2 projection.
+// Phase 1 (one thread per 5D site of the CTA): for each of the 8 directions the
+// neighbour column is loaded once (3 x 16 bytes = 4 spins of each colour), projected with
+// (1 - sig gamma_mu) in 16-bit pairs -- upper spins h = psi_u - sig X_mu psi_d, lower spins
+// -sig X_mu^+ h -- and scaled by norm_d / ref, ref = the largest of the 8 neighbour norms
+// of that column, so that all 8 directions can share one accumulator.  The four spin rows
+// [re,im of 3 colours, 0, 0] (16 bytes each) go to shared memory in ldmatrix row order.
+// Phase 2 (warps): a task is 4 columns x 4 spins = 16 rows of one site; for each
+// forward/backward pair of directions one ldmatrix.x4 gives the A fragment
+// (K = 2 directions x 8) and one mma adds U_mu(x) and U_mu(x-mu)^+ (B, built once per
+// site as real 6x6 blocks, K = input colour re/im, N = output colour re/im).  The FP32
+// result times ref is the hop of those 5D sites; the shared epilogue takes it from there.
+// Products of 16-bit inputs are exact in FP32 and sums are FP32; the extra rounding over
+// an FP32 evaluation is that of the 16-bit projection and of the norm ratio.
 #include "mdwf_impl.cuh"
 #include "mdwf_kernels.h"
 #include "mdwf_epi.cuh"
@@ -66,164 +61,212 @@ __device__ __forceinline__ uint32_t hfma2u(uint32_t a, uint32_t m, uint32_t c) {
   return *(uint32_t*)&r;
 }
 
-// Per-lane constants of one direction mu for slot j.
-struct DirConst {
-  uint32_t mf, mb;   // f16x2 multipliers of the partner spin for sig = +1 (forward) / -1
-  float zf, zb;      // lower-spin coefficient magnitude*sign for sig = +1 / -1
-};
-
-// Loads of one direction for the two rows of a lane (columns colA, colB of the tile).
-struct DirLoad {
-  uint4 qa, qb;
-  float na, nb;
-};
-
 template <int P>
-__device__ __forceinline__ void tc_load(DirLoad& L, const uint4* __restrict__ chunks, const float* __restrict__ norms,
-                                        int nbr, int W, int WN, int t, int colA, int colB, bool vA, bool vB) {
-  const uint4* pc = chunks + ((long long)nbr * 3 + t) * W;
-  L.qa = make_uint4(0, 0, 0, 0);
-  L.qb = make_uint4(0, 0, 0, 0);
-  L.na = 0.f;
-  L.nb = 0.f;
-  if (vA) {
-    L.qa = __ldg(pc + colA);
-    L.na = (P == F16) ? __ldg(norms + (long long)nbr * WN + colA) : 1.f;
-  }
-  if (vB) {
-    L.qb = __ldg(pc + colB);
-    L.nb = (P == F16) ? __ldg(norms + (long long)nbr * WN + colB) : 1.f;
+__device__ __forceinline__ void mma16n8k16(float d[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+  if constexpr (P == F16) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+  } else {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
   }
 }
 
-// One direction: project the two rows, mma, accumulate.
-template <int P, int MU, bool FWD, bool DAG>
-__device__ __forceinline__ void tc_dir(const DirLoad& L, int j, uint32_t bfrag, const DirConst& k, float up[2][2],
-                                       float lo_s[2][2], float lo_w[2][2]) {
+__device__ __forceinline__ void ldsm_x4(uint32_t r[4], const void* smem_row) {
+  const unsigned addr = (unsigned)__cvta_generic_to_shared(smem_row);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr));
+}
+
+// x -> i x on an f16x2 / bf16x2 complex (re low, im high): (-im, re)
+__device__ __forceinline__ uint32_t times_i(uint32_t v) { return swap_halves(v) ^ 0x00008000u; }
+__device__ __forceinline__ uint32_t neg2(uint32_t v) { return v ^ 0x80008000u; }
+
+// Phase-1 work of one direction for one 5D site: project (1 - sig gamma_mu) psi of the
+// neighbour column in 16-bit pairs, scale by ratio = norm_d / ref and write the four spin
+// rows [colour re,im x 3, 0, 0] of 16 bytes each.
+template <int P, int MU, int SIG>
+__device__ __forceinline__ void stage_dir(const uint4 q[3], uint32_t ratio, uint4* rows) {
   using H2 = typename TC<P>::H2;
-  constexpr int SIG = (FWD != DAG) ? 1 : -1;   // (1 - sig gamma_mu)
-  const uint4 qa = L.qa, qb = L.qb;
-  const float na = L.na, nb = L.nb;
-  // slot j of spin pair: psi_j and its partner (3-j for x,y ; 2+j for z,t)
-  const uint32_t sa = j ? qa.y : qa.x, sb = j ? qb.y : qb.x;
-  uint32_t pa, pb;
-  if (MU <= 1) { pa = j ? qa.z : qa.w; pb = j ? qb.z : qb.w; }
-  else { pa = j ? qa.w : qa.z; pb = j ? qb.w : qb.z; }
-  if (MU == 0 || MU == 2) { pa = swap_halves(pa); pb = swap_halves(pb); }   // factor i
-  const uint32_t m = SIG > 0 ? k.mf : k.mb;
-  const uint32_t a0 = hfma2u<H2>(pa, m, sa);
-  const uint32_t a1 = hfma2u<H2>(pb, m, sb);
-  float d[4];
-  mma16n8k8<P>(d, a0, a1, bfrag);
-  // upper spin j
-  up[0][0] = fmaf(na, d[0], up[0][0]); up[0][1] = fmaf(na, d[1], up[0][1]);
-  up[1][0] = fmaf(nb, d[2], up[1][0]); up[1][1] = fmaf(nb, d[3], up[1][1]);
-  // lower spin: x,y -> spin 1-j (swap), z,t -> spin j (same); zeta real (y,t) or imaginary (x,z)
-  const float z = SIG > 0 ? k.zf : k.zb;
-  const float wa = z * na, wb = z * nb;
-  float(*lo)[2] = (MU <= 1) ? lo_w : lo_s;
-  if (MU == 0 || MU == 2) {  // zeta = z i : (re, im) -> (-z im, z re)
-    lo[0][0] = fmaf(-wa, d[1], lo[0][0]); lo[0][1] = fmaf(wa, d[0], lo[0][1]);
-    lo[1][0] = fmaf(-wb, d[3], lo[1][0]); lo[1][1] = fmaf(wb, d[2], lo[1][1]);
-  } else {
-    lo[0][0] = fmaf(wa, d[0], lo[0][0]); lo[0][1] = fmaf(wa, d[1], lo[0][1]);
-    lo[1][0] = fmaf(wb, d[2], lo[1][0]); lo[1][1] = fmaf(wb, d[3], lo[1][1]);
+  // per-colour constants of h_j = psi_j + sig*kappa_j psi_partner
+  const uint32_t one_pm = TC<P>::h2((float)SIG, (float)-SIG);   // (sig, -sig)
+  const uint32_t mp_pm = TC<P>::h2((float)-SIG, (float)SIG);    // (-sig, sig)
+  const uint32_t s_neg = TC<P>::h2((float)-SIG, (float)-SIG);   // (-sig, -sig)
+  const uint32_t s_pos = TC<P>::h2((float)SIG, (float)SIG);     // (sig, sig)
+  uint32_t v[4][3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const uint32_t w0 = (&q[c].x)[0], w1 = (&q[c].x)[1], w2 = (&q[c].x)[2], w3 = (&q[c].x)[3];
+    uint32_t h0, h1;
+    if (MU == 0) {        // h0 = w0 - sig i w3 ; h1 = w1 - sig i w2
+      h0 = hfma2u<H2>(swap_halves(w3), one_pm, w0);
+      h1 = hfma2u<H2>(swap_halves(w2), one_pm, w1);
+    } else if (MU == 1) { // h0 = w0 - sig w3 ; h1 = w1 + sig w2
+      h0 = hfma2u<H2>(w3, s_neg, w0);
+      h1 = hfma2u<H2>(w2, s_pos, w1);
+    } else if (MU == 2) { // h0 = w0 - sig i w2 ; h1 = w1 + sig i w3
+      h0 = hfma2u<H2>(swap_halves(w2), one_pm, w0);
+      h1 = hfma2u<H2>(swap_halves(w3), mp_pm, w1);
+    } else {              // h0 = w0 - sig w2 ; h1 = w1 - sig w3
+      h0 = hfma2u<H2>(w2, s_neg, w0);
+      h1 = hfma2u<H2>(w3, s_neg, w1);
+    }
+    if (P == F16) {
+      H2 a = __hmul2(*(const H2*)&h0, *(const H2*)&ratio);
+      H2 b = __hmul2(*(const H2*)&h1, *(const H2*)&ratio);
+      h0 = *(uint32_t*)&a;
+      h1 = *(uint32_t*)&b;
+    }
+    // lower spins = -sig X_mu^+ h
+    uint32_t l0, l1;
+    if (MU == 0) {        // l0 = sig i h1 ; l1 = sig i h0
+      l0 = times_i(h1); l1 = times_i(h0);
+      if (SIG < 0) { l0 = neg2(l0); l1 = neg2(l1); }
+    } else if (MU == 1) { // l0 = sig h1 ; l1 = -sig h0
+      l0 = SIG > 0 ? h1 : neg2(h1); l1 = SIG > 0 ? neg2(h0) : h0;
+    } else if (MU == 2) { // l0 = sig i h0 ; l1 = -sig i h1
+      l0 = times_i(h0); l1 = times_i(h1);
+      if (SIG > 0) l1 = neg2(l1); else l0 = neg2(l0);
+    } else {              // l0 = -sig h0 ; l1 = -sig h1
+      l0 = SIG > 0 ? neg2(h0) : h0; l1 = SIG > 0 ? neg2(h1) : h1;
+    }
+    v[0][c] = h0; v[1][c] = h1; v[2][c] = l0; v[3][c] = l1;
   }
+#pragma unroll
+  for (int k = 0; k < 4; k++) rows[k] = make_uint4(v[k][0], v[k][1], v[k][2], 0u);
+}
+
+// Shared memory carve of the mma hop: A rows, per-column scale, neighbour table, epilogue.
+struct MmaSmem {
+  size_t a_off, ref_off, nbr_off, tile_off, red_off, total;
+};
+__host__ __device__ inline MmaSmem mma_smem(int ns, int nrhs, int Ls, bool center, int threads) {
+  MmaSmem m;
+  const size_t W = (size_t)nrhs * Ls;
+  m.a_off = 0;
+  m.ref_off = m.a_off + (size_t)ns * 8 * W * 4 * 16;
+  m.nbr_off = m.ref_off + ((ns * W * 4 + 15) & ~(size_t)15);
+  m.tile_off = m.nbr_off + ((size_t)ns * 8 * 4 + 15) / 16 * 16;
+  const size_t tile = (size_t)ns * nrhs * tile_gstr(Ls) * 4;
+  m.red_off = m.tile_off + ((tile * (center ? 2 : 1) + 15) & ~(size_t)15);
+  const size_t nsites = (size_t)ns * W;
+  m.total = m.red_off + ((nsites > (size_t)threads ? nsites : (size_t)threads) + (size_t)ns * nrhs) * 8 + 16;
+  return m;
 }
 
 template <int P, bool DAG>
-__global__ void __launch_bounds__(256) hop_tc_kernel(const __grid_constant__ HopParams p) {
-  using H2 = typename TC<P>::H2;
+__global__ void __launch_bounds__(256) hop_mma_kernel(const __grid_constant__ HopParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int Ls = p.in.Ls, nrhs = p.in.nrhs, W = Ls * nrhs, LsP = Ls + 1;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int ns = blockDim.x >> 5;
-  const int g = lane >> 2, t = lane & 3, j = g & 1;
-  const int ngrp = ns * nrhs;
-  float* tileH = (float*)smem_raw;
-  float* tileC = tileH + ngrp * 24 * LsP;
-  const size_t toff = ((size_t)ngrp * 24 * LsP * sizeof(float) * (p.has_center ? 2 : 1) + 15) & ~(size_t)15;
-  double* redsm = (double*)(smem_raw + toff);
-  const long long x_cb = (long long)blockIdx.x * ns + warp;
+  const int Ls = p.in.Ls, nrhs = p.in.nrhs, W = Ls * nrhs, GS = tile_gstr(Ls);
+  const int ns = p.ns, nt = blockDim.x, tid = threadIdx.x;
+  const long long site0 = (long long)blockIdx.x * ns;
+  const MmaSmem L = mma_smem(ns, nrhs, Ls, p.has_center, nt);
+  uint4* Abuf = (uint4*)(smem_raw + L.a_off);
+  float* ref = (float*)(smem_raw + L.ref_off);
+  int* nbrs = (int*)(smem_raw + L.nbr_off);
+  float* tileH = (float*)(smem_raw + L.tile_off);
+  float* tileC = tileH + ns * nrhs * GS;
+  double* redsm = (double*)(smem_raw + L.red_off);
 
-  if (x_cb < p.g.vh) {
+  // phase 0: neighbour table of the CTA's sites
+  for (int i = tid; i < ns * 8; i += nt) {
+    const long long x = site0 + i / 8;
+    if (x >= p.g.vh) continue;
     int c[4];
-    cb_coords(p.g, x_cb, p.pout, c);
-    int nbr[8];
-#pragma unroll
-    for (int mu = 0; mu < 4; mu++) {
-      nbr[mu] = (int)nbr_cb(p.g, c, mu, +1);
-      nbr[4 + mu] = (int)nbr_cb(p.g, c, mu, -1);
-    }
-    // B fragments: lane (g, t) holds (k = 2t, 2t+1 ; n = g) of U_d embedded as real 6x6:
-    // output re: (Re U[c][t], -Im U[c][t]) ; output im: (Im U[c][t], Re U[c][t]), c = g/2
-    uint32_t bfr[8];
-    const uint32_t* gl = (const uint32_t*)((const __half*)p.gauge + x_cb * 8 * p.gs);
+    cb_coords(p.g, x, p.pout, c);
+    const int d = i & 7;
+    nbrs[i] = (int)nbr_cb(p.g, c, d & 3, d < 4 ? +1 : -1);
+  }
+  __syncthreads();
+
+  // phase 1: one thread per 5D site stages the 8 directions' projected rows
+  const uint4* chunks = (const uint4*)p.in.data;
+  for (int i = tid; i < ns * W; i += nt) {
+    const int site_l = i / W, col = i - site_l * W;
+    if (site0 + site_l >= p.g.vh) continue;
+    const int* nb = nbrs + site_l * 8;
+    float nv[8];
+    float mx = 0.f;
 #pragma unroll
     for (int d = 0; d < 8; d++) {
-      uint32_t u = 0;
-      if (g < 6 && t < 3) u = __ldg(gl + (d * p.gs) / 2 + (g >> 1) * 3 + t);
-      bfr[d] = (g < 6 && t < 3) ? (j ? swap_halves(u) : (u ^ 0x80000000u)) : 0u;
+      nv[d] = (P == F16) ? __ldg(p.in.norm + (long long)nb[d] * W + col) : 1.f;
+      mx = fmaxf(mx, nv[d]);
     }
-    // per-lane projection / reconstruction constants (see header): kappa for slot j,
-    // half2 multiplier of the (possibly swapped) partner for sig = +1 / -1
-    DirConst kc[4];
+    ref[i] = mx;
+    const float inv = mx > 0.f ? 1.f / mx : 0.f;
+    uint4* rows = Abuf + ((size_t)site_l * 8 * W + col) * 4;
+#define STAGE(D, MU, SIG)                                                                 \
+    {                                                                                     \
+      const uint4* pc = chunks + (long long)nb[D] * 3 * W + col;                          \
+      uint4 q[3] = {__ldg(pc), __ldg(pc + W), __ldg(pc + 2 * W)};                         \
+      const uint32_t ratio = TC<P>::h2(nv[D] * inv, nv[D] * inv);                         \
+      stage_dir<P, MU, SIG>(q, ratio, rows + (size_t)(D) * W * 4);                        \
+    }
+    constexpr int SF = DAG ? -1 : 1;
+    STAGE(0, 0, SF) STAGE(1, 1, SF) STAGE(2, 2, SF) STAGE(3, 3, SF)
+    STAGE(4, 0, -SF) STAGE(5, 1, -SF) STAGE(6, 2, -SF) STAGE(7, 3, -SF)
+#undef STAGE
+  }
+  __syncthreads();
+
+  // phase 2: a warp takes whole sites; per 4-column tile: 16 rows = 4 columns x 4 spins,
+  // K = 2 directions (forward/backward of one mu) per mma
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int ntile = (W + 3) >> 2;
+  const int m = lane >> 3, rr = lane & 7;            // ldmatrix: matrix m, row rr
+  const int rho = (m & 1) * 8 + rr;                  // row within the tile
+  for (int site_l = warp; site_l < ns; site_l += nwarps) {
+    const long long x = site0 + site_l;
+    if (x >= p.g.vh) continue;
+    // B: lane (g, t) holds (k = 2t, 2t+1 ; n = g) of U_d as a real 6x6 block:
+    // output re: (Re U[c][t], -Im U[c][t]), output im: (Im U[c][t], Re U[c][t]), c = g/2
+    uint32_t bfr[8];
     {
-      // kappa: x: -i, -i ; y: -1, +1 ; z: -i, +i ; t: -1, -1  ->  h = psi_j + sig kappa psi_p
-      // for an i-factor the partner is swapped (im, re) and multiplied by (-s, +s) * sig*kappa_i
-      const float kx = -1.f, ky = j ? 1.f : -1.f, kz = j ? 1.f : -1.f, kt = -1.f;
-      kc[0].mf = TC<P>::h2(-kx, kx);
-      kc[0].mb = TC<P>::h2(kx, -kx);
-      kc[1].mf = TC<P>::h2(ky, ky);
-      kc[1].mb = TC<P>::h2(-ky, -ky);
-      kc[2].mf = TC<P>::h2(-kz, kz);
-      kc[2].mb = TC<P>::h2(kz, -kz);
-      kc[3].mf = TC<P>::h2(kt, kt);
-      kc[3].mb = TC<P>::h2(-kt, -kt);
-      // zeta = -sig X_mu^+ entry feeding the lower spin: x: sig i ; y: sig (j ? 1 : -1) ;
-      // z: sig (j ? -i : i) ; t: -sig
-      kc[0].zf = 1.f; kc[0].zb = -1.f;
-      kc[1].zf = j ? 1.f : -1.f; kc[1].zb = -kc[1].zf;
-      kc[2].zf = j ? -1.f : 1.f; kc[2].zb = -kc[2].zf;
-      kc[3].zf = -1.f; kc[3].zb = 1.f;
+      const uint32_t* gl = (const uint32_t*)((const __half*)p.gauge + x * 8 * p.gs);
+#pragma unroll
+      for (int d = 0; d < 8; d++) {
+        uint32_t u = 0;
+        if (g < 6 && t < 3) u = __ldg(gl + (d * p.gs) / 2 + (g >> 1) * 3 + t);
+        bfr[d] = (g < 6 && t < 3) ? ((g & 1) ? swap_halves(u) : (u ^ 0x80000000u)) : 0u;
+      }
     }
-    const uint4* chunks = (const uint4*)p.in.data;
-    const float* norms = p.in.norm;
-    const int WN = W;
-    const int nct = (W + 7) >> 3;
-    for (int tile = 0; tile < nct; tile++) {
-      const int colA = tile * 8 + (g >> 1), colB = colA + 4;
-      const bool vA = colA < W && t < 3, vB = colB < W && t < 3;
-      float up[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, ls[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, lw[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-      // all eight directions' loads first, so one memory latency covers the tile
-      DirLoad L[8];
+    const uint4* abase_site = Abuf + (size_t)site_l * 8 * W * 4;
+    const float* ref_site = ref + site_l * W;
+    // output rows of this lane: column 2*rw + g/4 of the tile, spin g%4; track (rhs, s)
+    int oc[2] = {g >> 2, 2 + (g >> 2)};
+    int orr[2], os[2];
 #pragma unroll
-      for (int d = 0; d < 8; d++) tc_load<P>(L[d], chunks, norms, nbr[d], W, WN, t, colA, colB, vA, vB);
-      tc_dir<P, 0, true, DAG>(L[0], j, bfr[0], kc[0], up, ls, lw);
-      tc_dir<P, 0, false, DAG>(L[4], j, bfr[4], kc[0], up, ls, lw);
-      tc_dir<P, 1, true, DAG>(L[1], j, bfr[1], kc[1], up, ls, lw);
-      tc_dir<P, 1, false, DAG>(L[5], j, bfr[5], kc[1], up, ls, lw);
-      tc_dir<P, 2, true, DAG>(L[2], j, bfr[2], kc[2], up, ls, lw);
-      tc_dir<P, 2, false, DAG>(L[6], j, bfr[6], kc[2], up, ls, lw);
-      tc_dir<P, 3, true, DAG>(L[3], j, bfr[3], kc[3], up, ls, lw);
-      tc_dir<P, 3, false, DAG>(L[7], j, bfr[7], kc[3], up, ls, lw);
-      // lower spin 2+j of a column = own "same" part + partner slot's "swap" part
-      float lo[2][2];
+    for (int rw = 0; rw < 2; rw++) { orr[rw] = oc[rw] / Ls; os[rw] = oc[rw] - orr[rw] * Ls; }
+    const int spin = g & 3;
+    for (int tile = 0; tile < ntile; tile++) {
+      int colr = tile * 4 + (rho >> 2);
+      colr = colr < W ? colr : W - 1;   // rows past the last column read a valid row; unused
+      const uint4* abase = abase_site + (size_t)colr * 4 + (rho & 3);
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int rw = 0; rw < 2; rw++)
-#pragma unroll
-        for (int q = 0; q < 2; q++) lo[rw][q] = ls[rw][q] + __shfl_xor_sync(0xffffffffu, lw[rw][q], 4);
+      for (int ks = 0; ks < 4; ks++) {
+        const int dsel = (m >> 1) ? ks + 4 : ks;
+        uint32_t a[4];
+        ldsm_x4(a, abase + (size_t)dsel * W * 4);
+        mma16n8k16<P>(acc, a, bfr[ks], bfr[ks + 4]);
+      }
 #pragma unroll
       for (int rw = 0; rw < 2; rw++) {
-        const int col = rw ? colB : colA;
+        const int col = tile * 4 + oc[rw];
         if (col < W && t < 3) {
-          const int r = col / Ls, s = col - r * Ls, grp = warp * nrhs + r;
-          float* th = tileH + grp * 24 * LsP + s;
-          th[(2 * (t * 4 + j)) * LsP] = up[rw][0];
-          th[(2 * (t * 4 + j) + 1) * LsP] = up[rw][1];
-          th[(2 * (t * 4 + 2 + j)) * LsP] = lo[rw][0];
-          th[(2 * (t * 4 + 2 + j) + 1) * LsP] = lo[rw][1];
+          const float sc = ref_site[col];
+          float* th = tileH + (site_l * nrhs + orr[rw]) * GS + os[rw] * TSTR + 2 * (t * 4 + spin);
+          th[0] = acc[2 * rw] * sc;
+          th[1] = acc[2 * rw + 1] * sc;
         }
+        os[rw] += 4;
+        while (os[rw] >= Ls) { os[rw] -= Ls; orr[rw]++; }
       }
     }
   }
@@ -234,27 +277,33 @@ __global__ void __launch_bounds__(256) hop_tc_kernel(const __grid_constant__ Hop
 bool hop_tc_supported(int prec, const HopParams& p, bool r12) {
   if (r12 || (prec != F16 && prec != BF16)) return false;
   if (p.gs != 24) return false;
-  if (p.g.vh >= (1LL << 31) / 8) return false;
+  if (p.g.vh * 3 * (long long)p.in.nrhs * p.in.Ls >= (1LL << 31)) return false;
   return true;
+}
+
+static int tc_threads(const HopParams& p) {
+  const int W = p.in.nrhs * p.in.Ls;
+  int t = ((p.ns * W + 31) / 32) * 32;
+  return t < 64 ? 64 : (t > 256 ? 256 : t);
+}
+
+size_t hop_tc_smem_bytes(const HopParams& p) {
+  return mma_smem(p.ns, p.in.nrhs, p.in.Ls, p.has_center, tc_threads(p)).total;
 }
 
 template <int P, bool DAG>
 static cudaError_t go_tc(const HopParams& p, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(hop_tc_kernel<P, DAG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(hop_mma_kernel<P, DAG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const int threads = p.ns * 32;
-  const size_t smem = epi_smem_bytes(4, p.ns, p.in.nrhs, p.in.Ls, p.has_center, threads);
+  const int threads = tc_threads(p);
+  const size_t smem = hop_tc_smem_bytes(p);
   const long long blocks = (p.g.vh + p.ns - 1) / p.ns;
-  hop_tc_kernel<P, DAG><<<(unsigned)blocks, threads, smem, st>>>(p);
+  hop_mma_kernel<P, DAG><<<(unsigned)blocks, threads, smem, st>>>(p);
   return cudaGetLastError();
-}
-
-size_t hop_tc_smem_bytes(const HopParams& p) {
-  return epi_smem_bytes(4, p.ns, p.in.nrhs, p.in.Ls, p.has_center, p.ns * 32);
 }
 
 cudaError_t launch_hop_tc(int prec, bool dag, bool /*epi*/, const HopParams& p, cudaStream_t st) {

@@ -1,5 +1,6 @@
 // Shared epilogue of the fused hop kernels.  On entry tileH holds the hop result of every
-// 5D site of the CTA's ns 4D sites, laid out [grp = site_l * nrhs + r][24 reals][Ls + 1];
+// 5D site of the CTA's ns 4D sites, laid out [grp = site_l * nrhs + r][s][24 reals]
+// (strides tile_gstr(Ls) and TSTR);
 // the epilogue computes   out = fin( cc * cop(center) + hc * post(hop) )
 // (post/cop/fin: s-direction chains of D5, A5, A5^-1 and adjoints), optionally reduces
 // |out|^2 before fin, and either stores out or does r -= alpha out with |r|^2.
@@ -13,7 +14,8 @@ template <int P>
 __device__ __forceinline__ void hop_epilogue(const HopParams& p, typename PT<P>::C* tileH,
                                              typename PT<P>::C* tileC, double* redsm, int ns) {
   using C = typename PT<P>::C;
-  const int Ls = p.in.Ls, nrhs = p.in.nrhs, W = Ls * nrhs, LsP = Ls + 1;
+  const int Ls = p.in.Ls, nrhs = p.in.nrhs, W = Ls * nrhs;
+  const int GS = tile_gstr(Ls);
   const int tid = threadIdx.x, nt = blockDim.x;
   const long long site0 = (long long)blockIdx.x * ns;
   const int nsites = ns * W;
@@ -26,7 +28,7 @@ __device__ __forceinline__ void hop_epilogue(const HopParams& p, typename PT<P>:
       C v[24];
       load_site<P>(p.center, site0 + site_l, col, v);
 #pragma unroll
-      for (int k = 0; k < 24; k++) tileC[(grp * 24 + k) * LsP + s] = v[k];
+      for (int k = 0; k < 24; k++) tileC[grp * GS + s * TSTR + k] = v[k];
     }
     __syncthreads();
   }
@@ -34,15 +36,15 @@ __device__ __forceinline__ void hop_epilogue(const HopParams& p, typename PT<P>:
   const C hc = (C)p.hc, cc = (C)p.cc;
   for (int it = tid; it < nitems; it += nt) {
     const int g = it / 24, comp = it - g * 24;
-    if (site0 + g / nrhs >= p.g.vh) continue;
-    C* h = tileH + it * LsP;
-    chain_apply(p.post, comp, h, 1, Ls, mf);
+    if (site0 + (nrhs == 1 ? g : g / nrhs) >= p.g.vh) continue;
+    C* h = tileH + g * GS + comp;
+    if (p.post.op[0].kind != SOP_NONE) chain_apply_fast(p.post, comp, h, TSTR, Ls, mf);
     if (p.has_center) {
-      C* cv = tileC + it * LsP;
-      chain_apply(p.cop, comp, cv, 1, Ls, mf);
-      for (int ss = 0; ss < Ls; ss++) h[ss] = cc * cv[ss] + hc * h[ss];
+      C* cv = tileC + g * GS + comp;
+      if (p.cop.op[0].kind != SOP_NONE) chain_apply_fast(p.cop, comp, cv, TSTR, Ls, mf);
+      for (int ss = 0; ss < Ls; ss++) h[ss * TSTR] = cc * cv[ss * TSTR] + hc * h[ss * TSTR];
     } else if (p.hc != 1.0) {
-      for (int ss = 0; ss < Ls; ss++) h[ss] = hc * h[ss];
+      for (int ss = 0; ss < Ls; ss++) h[ss * TSTR] = hc * h[ss * TSTR];
     }
   }
   __syncthreads();
@@ -53,7 +55,7 @@ __device__ __forceinline__ void hop_epilogue(const HopParams& p, typename PT<P>:
       C n = 0;
       if (site0 + site_l < p.g.vh) {
 #pragma unroll
-        for (int k = 0; k < 24; k++) { C v = tileH[(grp * 24 + k) * LsP + s]; n += v * v; }
+        for (int k = 0; k < 24; k++) { C v = tileH[grp * GS + s * TSTR + k]; n += v * v; }
       }
       redsm[i] = (double)n;
     }
@@ -63,7 +65,7 @@ __device__ __forceinline__ void hop_epilogue(const HopParams& p, typename PT<P>:
     for (int it = tid; it < nitems; it += nt) {
       const int g = it / 24, comp = it - g * 24;
       if (site0 + g / nrhs >= p.g.vh) continue;
-      chain_apply(p.fin, comp, tileH + it * LsP, 1, Ls, mf);
+      chain_apply_fast(p.fin, comp, tileH + g * GS + comp, TSTR, Ls, mf);
     }
     __syncthreads();
   }
@@ -75,7 +77,7 @@ __device__ __forceinline__ void hop_epilogue(const HopParams& p, typename PT<P>:
     if (x < p.g.vh) {
       C v[24];
 #pragma unroll
-      for (int k = 0; k < 24; k++) v[k] = tileH[(grp * 24 + k) * LsP + s];
+      for (int k = 0; k < 24; k++) v[k] = tileH[grp * GS + s * TSTR + k];
       if (p.axpy_r) {
         C rv[24];
         load_site<P>(p.raxpy, x, col, rv);
@@ -96,7 +98,7 @@ __device__ __forceinline__ void hop_epilogue(const HopParams& p, typename PT<P>:
 
 // shared memory of the fused epilogue: tile(s) + reduction scratch
 __host__ __device__ inline size_t epi_smem_bytes(size_t csz, int ns, int nrhs, int Ls, bool center, int threads) {
-  const size_t tile = (size_t)ns * nrhs * 24 * (Ls + 1) * csz;
+  const size_t tile = (size_t)ns * nrhs * tile_gstr(Ls) * csz;
   const size_t nsites = (size_t)ns * nrhs * Ls;
   const size_t red = ((nsites > (size_t)threads ? nsites : (size_t)threads) + (size_t)ns * nrhs) * sizeof(double);
   return ((tile * (center ? 2 : 1) + 15) & ~(size_t)15) + red + 16;

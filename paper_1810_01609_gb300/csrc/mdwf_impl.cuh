@@ -245,6 +245,78 @@ __device__ __forceinline__ void chain_apply(const SChain& ch, int comp, C* y, in
   }
 }
 
+// Compile-time-Ls version: the column lives in registers, every loop is unrolled.
+template <typename C, int L>
+__device__ __forceinline__ void sop_col(const SOp& o, bool up, C (&y)[L], C mf) {
+  if (o.kind == SOP_BIDIAG) {
+    const C a = (C)o.a, b = (C)o.b;
+    if (up) {
+      const C y0 = y[0];
+#pragma unroll
+      for (int s = 0; s < L - 1; s++) y[s] = a * y[s] + b * y[s + 1];
+      y[L - 1] = a * y[L - 1] - b * mf * y0;
+    } else {
+      const C yl = y[L - 1];
+#pragma unroll
+      for (int s = L - 1; s > 0; s--) y[s] = a * y[s] + b * y[s - 1];
+      y[0] = a * y[0] - b * mf * yl;
+    }
+  } else if (o.kind == SOP_INV) {
+    const C inv_a = (C)o.inv_a, b = (C)o.b;
+    if (up) {
+      C acc = (C)o.c0 * y[L - 1];
+#pragma unroll
+      for (int j = 0; j < L - 1; j++) acc += (C)o.w[j] * y[j];
+      y[L - 1] = acc;
+#pragma unroll
+      for (int s = L - 2; s >= 0; s--) { acc = (y[s] - b * acc) * inv_a; y[s] = acc; }
+    } else {
+      C acc = (C)o.c0 * y[0];
+#pragma unroll
+      for (int j = 0; j < L - 1; j++) acc += (C)o.w[j] * y[L - 1 - j];
+      y[0] = acc;
+#pragma unroll
+      for (int s = 1; s < L; s++) { acc = (y[s] - b * acc) * inv_a; y[s] = acc; }
+    }
+  }
+}
+
+template <typename C, int L>
+__device__ __forceinline__ void chain_col(const SChain& ch, bool lower, C* col, int st, C mf) {
+  C y[L];
+#pragma unroll
+  for (int s = 0; s < L; s++) y[s] = col[s * st];
+#pragma unroll
+  for (int i = 0; i < 2; i++) {
+    if (ch.op[i].kind == SOP_NONE) continue;
+    sop_col<C, L>(ch.op[i], (!lower) != (bool)ch.op[i].dag, y, mf);
+  }
+#pragma unroll
+  for (int s = 0; s < L; s++) col[s * st] = y[s];
+}
+
+// chain on one strided column in shared memory: unrolled register code for Ls <= 16
+template <typename C>
+__device__ __forceinline__ void chain_apply_fast(const SChain& ch, int comp, C* col, int st, int Ls, C mf) {
+  const bool lower = ((comp >> 1) & 3) >= 2;
+  switch (Ls) {
+#define CASE_L(L) case L: chain_col<C, L>(ch, lower, col, st, mf); return;
+    CASE_L(2) CASE_L(3) CASE_L(4) CASE_L(5) CASE_L(6) CASE_L(7) CASE_L(8) CASE_L(9)
+    CASE_L(10) CASE_L(11) CASE_L(12) CASE_L(13) CASE_L(14) CASE_L(15) CASE_L(16)
+#undef CASE_L
+    default: chain_apply(ch, comp, col, st, Ls, mf);
+  }
+}
+
+// Epilogue tile layout [grp = site * nrhs + rhs][s][component]: 24 components padded to
+// TSTR per s (16-byte aligned rows, conflict-free 16-byte accesses), groups padded so
+// that consecutive groups start 24 banks apart (conflict-free column walks).
+constexpr int TSTR = 28;
+__host__ __device__ inline int tile_gstr(int Ls) {
+  const int base = Ls * TSTR;
+  return base + ((24 - (base & 31)) & 31);
+}
+
 // ---------------------------------------------------------------- reductions
 // Block partials -> last block sums them in a fixed order (deterministic) and runs a
 // scalar program.  partials[block * nrhs + r], counter reset by the last block.

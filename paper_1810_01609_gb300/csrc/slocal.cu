@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(MAXTHREADS) chain_kernel(const __grid_constant
   const int nitems = p.ns * nrhs * 24;
   for (int it = tid; it < nitems; it += blockDim.x) {
     if ((long long)blockIdx.x * p.ns + (it / 24) / nrhs >= p.vh) continue;
-    chain_apply(p.chain, it % 24, tile + it * LsP, 1, Ls, (C)p.mf);
+    chain_apply_fast(p.chain, it % 24, tile + it * LsP, 1, Ls, (C)p.mf);
   }
   __syncthreads();
   if (active) {
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(MAXTHREADS) cg_update_kernel(const __grid_cons
   const int nitems = p.ns * nrhs * 24;
   for (int it = tid; it < nitems; it += blockDim.x) {
     if ((long long)blockIdx.x * p.ns + (it / 24) / nrhs >= p.vh) continue;
-    chain_apply(p.chain, it % 24, tile + it * LsP, 1, Ls, (C)p.mf);
+    chain_apply_fast(p.chain, it % 24, tile + it * LsP, 1, Ls, (C)p.mf);
   }
   __syncthreads();
   if (active) {
