@@ -34,8 +34,14 @@ __device__ __forceinline__ void hop_epilogue(const HopParams& p, typename PT<P>:
   }
   const int nitems = ns * nrhs * 24;
   const C hc = (C)p.hc, cc = (C)p.cc;
-  for (int it = tid; it < nitems; it += nt) {
-    const int g = it / 24, comp = it - g * 24;
+  // items chirality-major (all upper-spin columns, then all lower-spin ones): the two
+  // chiralities walk s in opposite directions, so a warp stays on one code path
+  const int nhalf = ns * nrhs * 12;
+  for (int it2 = tid; it2 < nitems; it2 += nt) {
+    const int lowerh = it2 >= nhalf;
+    const int j = lowerh ? it2 - nhalf : it2;
+    const int g = j / 12, q = j - g * 12;                         // q: colour (q / 4), spin pair, re/im
+    const int comp = 8 * (q >> 2) + 4 * lowerh + (q & 3);
     if (site0 + (nrhs == 1 ? g : g / nrhs) >= p.g.vh) continue;
     C* h = tileH + g * GS + comp;
     if (p.post.op[0].kind != SOP_NONE) chain_apply_fast(p.post, comp, h, TSTR, Ls, mf);
@@ -62,9 +68,12 @@ __device__ __forceinline__ void hop_epilogue(const HopParams& p, typename PT<P>:
   }
   if (p.fin.op[0].kind != SOP_NONE) {
     __syncthreads();
-    for (int it = tid; it < nitems; it += nt) {
-      const int g = it / 24, comp = it - g * 24;
-      if (site0 + g / nrhs >= p.g.vh) continue;
+    for (int it2 = tid; it2 < nitems; it2 += nt) {
+      const int lowerh = it2 >= nhalf;
+      const int j = lowerh ? it2 - nhalf : it2;
+      const int g = j / 12, q = j - g * 12;
+      const int comp = 8 * (q >> 2) + 4 * lowerh + (q & 3);
+      if (site0 + (nrhs == 1 ? g : g / nrhs) >= p.g.vh) continue;
       chain_apply_fast(p.fin, comp, tileH + g * GS + comp, TSTR, Ls, mf);
     }
     __syncthreads();
