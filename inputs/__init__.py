@@ -86,3 +86,31 @@ def z2_source4d(dims, seed):
     X, Y, Z, T = dims
     r = _rng(seed).integers(0, 2, size=(T, Z, Y, X, 4, 3))
     return (1.0 - 2.0 * r).astype(np.complex128)
+
+
+def gaussian_spinor5d_device(dims, Ls, seed, nrhs=1, device="cuda"):
+    """Complex Gaussian 5D field [nrhs, s, t, z, y, x, 4, 3] drawn on the GPU with a seeded
+    torch Philox generator (for lattices whose complex128 fields do not fit host memory
+    comfortably).  Deterministic for a given seed, device type and torch version."""
+    import torch
+    X, Y, Z, T = dims
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    shape = (nrhs, Ls, T, Z, Y, X, 4, 3, 2)
+    r = torch.randn(shape, generator=g, device=device, dtype=torch.float64)
+    return torch.view_as_complex(r)
+
+
+class DeviceSites:
+    """Read-only numpy view of selected sites of a device field: field[..., t, z, y, x, :, :]
+    with integer index arrays fetches only those sites (what oracle.sample's gather does)."""
+
+    def __init__(self, tensor):
+        self.t = tensor
+
+    def __getitem__(self, idx):
+        import torch
+        if not (isinstance(idx, tuple) and idx[0] is Ellipsis):
+            raise IndexError("expected field[..., t, z, y, x, :, :]")
+        t, z, y, x = (torch.as_tensor(a, device=self.t.device) for a in idx[1:5])
+        return self.t[..., t, z, y, x, :, :].cpu().numpy()
