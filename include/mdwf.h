@@ -136,7 +136,7 @@ typedef struct mdwf_ctx mdwf_ctx;
 /* Fill *p with defaults: dims 4^4, Ls 8, b5 1.5, c5 0.5, M5 1.3, mf 0.05, t_bc -1,
  * recon 18, check_su3 1. */
 void mdwf_default_params(mdwf_params* p);
-/* Defaults: tol 1e-10, maxiter 100000, sloppy F16, delta 0.1, ru_interval 100,
+/* Defaults: tol 1e-10, maxiter 100000, sloppy F16, delta 0.05, ru_interval 100,
  * check_interval 10, use_graph 1, location DEVICE, full_residual 1. */
 void mdwf_default_solve_params(mdwf_solve_params* sp);
 
