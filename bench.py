@@ -35,7 +35,11 @@ WORKLOADS = {
     "16^3x32_Ls12": ((16, 16, 16, 32), 12, 0.02, 0.4, 2),
     "24^3x64_Ls10": ((24, 24, 24, 64), 10, 0.01, 0.5, 3),
     "4^4_Ls8": ((4, 4, 4, 4), 8, 0.05, 0.2, 1),
+    "32^3x64_Ls12": ((32, 32, 32, 64), 12, 0.01, 0.5, 4),
+    "48^3x96_Ls8": ((48, 48, 48, 96), 8, 0.005, 0.6, 5),
 }
+# extra modes (one JSON line each, not the default benchmark line)
+MODES = ("batch32", "large48", "graphbatch")
 METRIC = "MDWF Dslash HBM GB/s (% of peak); solve time to 1e-10, mixed vs FP64"
 
 
@@ -198,13 +202,168 @@ def kernel_only(args, m, ctx, dims, Ls, seed, stream):
                       "tune": ctx.tune_entries()}))
 
 
+def _setup_gpu():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1810_01609_gb300 as m
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    return torch, m, stream
+
+
+def mode_batch32(args):
+    """32^3x64, Ls 12: 12 spin-colour point sources -> multi-RHS mixed solves (groups of
+    --group right-hand sides per launch), Feynman-Hellmann sequential solves, nucleon 2-pt
+    and FH 3-pt (both u lines) contractions in FP64."""
+    torch, m, stream = _setup_gpu()
+    import inputs
+    dims, Ls, mf, eps, seed = WORKLOADS["32^3x64_Ls12"]
+    ctx = m.Context(dims, Ls, mf=mf)
+    t0 = time.perf_counter()
+    ctx.load_gauge(inputs.gauge_links(dims, eps, seed))
+    t_links = time.perf_counter() - t0
+    G = args.group
+    b4 = torch.stack([torch.from_numpy(inputs.point_source4d(dims, k // 3, k % 3)) for k in range(12)]).cuda()
+
+    def solve_cols(src4):
+        cols, its, rus, res = [], [], [], []
+        for g0 in range(0, 12, G):
+            eta = ctx.make_source_4d(src4[g0:g0 + G].contiguous(), nrhs=G, stream=stream)
+            y, infos = ctx.solve_multi(eta, sloppy=args.sloppy, tol=1e-10, full_residual=False, stream=stream)
+            del eta
+            cols.append(ctx.project_4d(y, nrhs=G, stream=stream))
+            del y
+            its += [i.iterations for i in infos]
+            rus += [i.reliable_updates for i in infos]
+            res += [i.true_residual for i in infos]
+        return torch.cat(cols), its, rus, res
+
+    torch.cuda.synchronize()
+    bytes0, launches0 = ctx.algorithmic_bytes(), ctx.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    S, its, rus, res = solve_cols(b4)
+    SF, its_f, rus_f, res_f = solve_cols(ctx.fh_source(S, nrhs=12, stream=stream))
+    C2 = ctx.contract_nucleon(S, S, S, stream=stream)
+    C3 = ctx.contract_nucleon(SF, S, S, stream=stream) + ctx.contract_nucleon(S, S, SF, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    nbytes = ctx.algorithmic_bytes() - bytes0
+    c2 = C2.cpu().numpy()
+    c3 = C3.cpu().numpy()
+    ratio = (c3[1:6] / c2[1:6]).real - (c3[0:5] / c2[0:5]).real
+    out = {"metric": METRIC, "value": nbytes / (ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": 1,
+           "warmup": 0, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f16+f32 (inner), f64", "data": "synthetic",
+           "config": {"workload": "batch32: 32^3x64 Ls12, 12 point sources + 12 FH sequential solves + contractions",
+                      "lattice": list(dims), "Ls": Ls, "mf": mf, "link_eps": eps, "seed": seed,
+                      "rhs_per_launch": G, "sloppy": args.sloppy, "tol": 1e-10},
+           "solve": {"iterations": its, "iterations_fh": its_f, "reliable_updates": rus,
+                     "max_true_residual": max(res + res_f)},
+           "nucleon_2pt_t0_4": [[float(z.real), float(z.imag)] for z in c2[:5]],
+           "fh_effective_ratio_t0_4": [float(v) for v in ratio],
+           "gpu_launches": int(ctx.launch_count() - launches0), "host_link_generation_s": t_links}
+    print(json.dumps(out))
+
+
+def mode_large48(args):
+    """48^3x96, Ls 8, m 0.005: one point-source mixed solve (links drawn on the device)."""
+    torch, m, stream = _setup_gpu()
+    import inputs
+    dims, Ls, mf, eps, seed = WORKLOADS["48^3x96_Ls8"]
+    ctx = m.Context(dims, Ls, mf=mf)
+    U = inputs.gauge_links_device(dims, eps, seed)
+    ctx.load_gauge(U, stream=stream)
+    del U
+    b4 = torch.from_numpy(inputs.point_source4d(dims, 0, 0)).cuda().reshape((1,) + ctx.shape4d())
+    eta = ctx.make_source_4d(b4, nrhs=1, stream=stream)[0]
+    ctx.solve(eta, sloppy=args.sloppy, tol=1e-10, maxiter=200, stream=stream)   # tuning, graphs
+    torch.cuda.synchronize()
+    bytes0 = ctx.algorithmic_bytes()
+    t0 = time.perf_counter()
+    x, info = ctx.solve(eta, sloppy=args.sloppy, tol=1e-10, stream=stream)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3
+    nbytes = ctx.algorithmic_bytes() - bytes0
+    out = {"metric": METRIC, "value": nbytes / (ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": 1,
+           "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f16+f32 (inner), f64", "data": "synthetic",
+           "config": {"workload": "large48: 48^3x96 Ls8 point-source solve", "lattice": list(dims), "Ls": Ls,
+                      "mf": mf, "link_eps": eps, "seed": seed, "links": "device Philox (inputs.gauge_links_device)",
+                      "sloppy": args.sloppy, "tol": 1e-10},
+           "solve": {"ms": ms, "iterations": info.iterations, "reliable_updates": info.reliable_updates,
+                     "true_residual": info.true_residual, "full_residual": info.full_residual},
+           "device_memory_peak_gb": torch.cuda.max_memory_allocated() / 1e9}
+    print(json.dumps(out))
+
+
+def mode_graphbatch(args):
+    """64 solves drawn uniformly from {8^3x16, 12^3x24, 16^3x32} x Ls {8, 12}, Z2-noise
+    sources, CG iterations replayed as captured graphs per shape; solves/s and p50/p99
+    latency, against the plain FP64 solver on the first --fp64-solves of the same draws."""
+    torch, m, stream = _setup_gpu()
+    import inputs
+    shapes = [(d, ls) for d in ((8, 8, 8, 16), (12, 12, 12, 24), (16, 16, 16, 32)) for ls in (8, 12)]
+    mf, eps, seed = 0.005, 0.6, 5
+    rng = np.random.default_rng(seed)
+    draws = rng.integers(0, len(shapes), size=64)
+    ctxs = {}
+    for k, (d, ls) in enumerate(shapes):
+        c = m.Context(d, ls, mf=mf)
+        c.load_gauge(inputs.gauge_links(d, eps, seed + 10 * k))
+        ctxs[k] = c
+
+    def src(i):
+        d, ls = shapes[draws[i]]
+        z = torch.from_numpy(inputs.z2_source4d(d, seed + 1000 + i)).cuda().reshape((1,) + ctxs[draws[i]].shape4d())
+        return ctxs[draws[i]].make_source_4d(z, nrhs=1, stream=stream)[0]
+
+    srcs = [src(i) for i in range(64)]
+    for k in ctxs:   # one warm solve per shape: tuning and graph capture
+        j = int(np.nonzero(draws == k)[0][0]) if np.any(draws == k) else None
+        if j is not None:
+            ctxs[k].solve(srcs[j], sloppy=args.sloppy, tol=1e-10, stream=stream)
+    torch.cuda.synchronize()
+    lat, its = [], []
+    t0 = time.perf_counter()
+    for i in range(64):
+        t = time.perf_counter()
+        x, info = ctxs[draws[i]].solve(srcs[i], sloppy=args.sloppy, tol=1e-10, stream=stream)
+        lat.append((time.perf_counter() - t) * 1e3)
+        its.append(info.iterations)
+    total = time.perf_counter() - t0
+    lat64 = []
+    for i in range(min(args.fp64_solves, 64)):
+        t = time.perf_counter()
+        ctxs[draws[i]].solve(srcs[i], sloppy="f64", tol=1e-10, stream=stream)
+        lat64.append((time.perf_counter() - t) * 1e3)
+    out = {"metric": METRIC, "value": 64 / total, "unit": "solves/s", "n_gpus": 1, "steps": 64, "warmup": len(ctxs),
+           "ms_per_step": total * 1e3 / 64, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f16+f32 (inner), f64", "data": "synthetic",
+           "config": {"workload": "graphbatch: 64 Z2-noise solves over 3 lattices x 2 Ls", "mf": mf, "link_eps": eps,
+                      "seed": seed, "sloppy": args.sloppy, "tol": 1e-10,
+                      "draw_counts": {"%dx%d_Ls%d" % (shapes[k][0][0], shapes[k][0][3], shapes[k][1]): int(np.sum(draws == k)) for k in range(len(shapes))}},
+           "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "mean": float(np.mean(lat))},
+           "fp64_latency_ms_first_%d" % len(lat64): {"p50": float(np.percentile(lat64, 50)), "p99": float(np.percentile(lat64, 99)),
+                                                     "mean": float(np.mean(lat64))},
+           "mixed_latency_ms_first_%d" % len(lat64): {"mean": float(np.mean(lat[:len(lat64)]))},
+           "iterations": {"min": int(min(its)), "max": int(max(its))}}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="16^3x32_Ls12", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="16^3x32_Ls12", choices=sorted(WORKLOADS) + list(MODES))
+    ap.add_argument("--group", type=int, default=3, help="batch32: right-hand sides per multi-RHS launch")
+    ap.add_argument("--fp64-solves", type=int, default=16, help="graphbatch: solves repeated with plain FP64")
     ap.add_argument("--sloppy", default="f16", choices=["f16", "bf16", "f32"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -216,7 +375,11 @@ def main():
     args = ap.parse_args()
     wl = args.workload
     if args.impl == "reference":
+        if wl in MODES:
+            wl = {"batch32": "32^3x64_Ls12", "large48": "48^3x96_Ls8", "graphbatch": "16^3x32_Ls12"}[wl]
         return run_reference(args, wl)
+    if wl in MODES:
+        return {"batch32": mode_batch32, "large48": mode_large48, "graphbatch": mode_graphbatch}[wl](args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -114,3 +114,31 @@ class DeviceSites:
             raise IndexError("expected field[..., t, z, y, x, :, :]")
         t, z, y, x = (torch.as_tensor(a, device=self.t.device) for a in idx[1:5])
         return self.t[..., t, z, y, x, :, :].cpu().numpy()
+
+
+def gauge_links_device(dims, eps, seed, device="cuda", chunk=1 << 22):
+    """Links [t,z,y,x,mu,3,3] (complex128, on the GPU) from the recipe of gauge_links, with
+    the Gaussian entries drawn by a seeded torch Philox generator on the device instead of
+    numpy (for lattices whose host generation would take minutes)."""
+    import torch
+    X, Y, Z, T = dims
+    n = X * Y * Z * T * 4
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    out = torch.empty((n, 3, 3), dtype=torch.complex128, device=device)
+    eye = torch.eye(3, dtype=torch.complex128, device=device)
+    for i in range(0, n, chunk):
+        m = min(chunk, n - i)
+        r = torch.randn((m, 3, 3, 2), generator=g, device=device, dtype=torch.float64)
+        a = torch.view_as_complex(r)
+        h = 0.5 * (a + a.conj().transpose(-1, -2))
+        tr = torch.diagonal(h, dim1=-2, dim2=-1).sum(-1).real / 3.0
+        h = h - tr[:, None, None] * eye
+        w, v = torch.linalg.eigh(h)
+        u = (v * torch.exp(1j * eps * w)[:, None, :]) @ v.conj().transpose(-1, -2)
+        r0 = u[:, 0, :] / torch.linalg.vector_norm(u[:, 0, :], dim=-1, keepdim=True)
+        r1 = u[:, 1, :] - (r0.conj() * u[:, 1, :]).sum(-1, keepdim=True) * r0
+        r1 = r1 / torch.linalg.vector_norm(r1, dim=-1, keepdim=True)
+        r2 = torch.linalg.cross(r0, r1).conj()
+        out[i:i + m] = torch.stack([r0, r1, r2], dim=1)
+    return out.reshape(T, Z, Y, X, 4, 3, 3)
