@@ -116,10 +116,11 @@ class DeviceSites:
         return self.t[..., t, z, y, x, :, :].cpu().numpy()
 
 
-def gauge_links_device(dims, eps, seed, device="cuda", chunk=1 << 22):
+def gauge_links_device(dims, eps, seed, device="cuda", chunk=1 << 16):
     """Links [t,z,y,x,mu,3,3] (complex128, on the GPU) from the recipe of gauge_links, with
     the Gaussian entries drawn by a seeded torch Philox generator on the device instead of
-    numpy (for lattices whose host generation would take minutes)."""
+    numpy and exp(i eps H) by the batched matrix exponential (for lattices whose host
+    generation would take minutes)."""
     import torch
     X, Y, Z, T = dims
     n = X * Y * Z * T * 4
@@ -134,8 +135,7 @@ def gauge_links_device(dims, eps, seed, device="cuda", chunk=1 << 22):
         h = 0.5 * (a + a.conj().transpose(-1, -2))
         tr = torch.diagonal(h, dim1=-2, dim2=-1).sum(-1).real / 3.0
         h = h - tr[:, None, None] * eye
-        w, v = torch.linalg.eigh(h)
-        u = (v * torch.exp(1j * eps * w)[:, None, :]) @ v.conj().transpose(-1, -2)
+        u = torch.linalg.matrix_exp(1j * eps * h)   # exp(i eps H), batched on the device
         r0 = u[:, 0, :] / torch.linalg.vector_norm(u[:, 0, :], dim=-1, keepdim=True)
         r1 = u[:, 1, :] - (r0.conj() * u[:, 1, :]).sum(-1, keepdim=True) * r0
         r1 = r1 / torch.linalg.vector_norm(r1, dim=-1, keepdim=True)

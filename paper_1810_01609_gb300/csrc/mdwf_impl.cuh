@@ -129,6 +129,10 @@ __device__ __forceinline__ void store_site(const Field& f, long long x_cb, int c
       float m = 0.0f;
 #pragma unroll
       for (int i = 0; i < 24; i++) m = fmaxf(m, fabsf(v[i]));
+      // a site whose largest component is below the smallest normal float stores zero
+      // (1/m would overflow); such entries are far below half-precision resolution of any
+      // field they belong to
+      if (!(m >= 1.17549435e-38f)) m = 0.0f;
       f.norm[x_cb * W + col] = m;
       scale = m > 0.0f ? 1.0f / m : 0.0f;
     }
