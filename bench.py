@@ -43,6 +43,33 @@ MODES = ("batch32", "large48", "graphbatch")
 METRIC = "MDWF Dslash HBM GB/s (% of peak); solve time to 1e-10, mixed vs FP64"
 
 
+def kernel_sources_hash():
+    """sha256 over the CUDA sources and the C header: identifies the kernels a stored ncu
+    capture belongs to."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1810_01609_gb300", "csrc")
+    files = sorted(f for f in os.listdir(csrc) if f.endswith((".cu", ".cuh", ".h")) and f != "probe_throughput.cu")
+    for name in files + ["../../include/mdwf.h"]:
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode())
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def stored_traffic(key):
+    """DRAM bytes per launch from profiles/roofline_traffic.json if it was captured on the
+    current kernel sources, else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
+            d = json.load(f)
+        if d.get("sources_sha256") != kernel_sources_hash():
+            return None
+        return d["entries"][key]["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -372,8 +399,12 @@ def main():
     ap.add_argument("--kernel-only", action="store_true",
                     help="only launch the fused hop + M5^-1 kernel a few times (for ncu captures)")
     ap.add_argument("--op", default="HOP_OE_M5INV")
+    ap.add_argument("--print-hash", action="store_true", help="print the kernel-source hash and exit")
     args = ap.parse_args()
     wl = args.workload
+    if args.print_hash:
+        print(kernel_sources_hash())
+        return
     if args.impl == "reference":
         if wl in MODES:
             wl = {"batch32": "32^3x64_Ls12", "large48": "48^3x96_Ls8", "graphbatch": "16^3x32_Ls12"}[wl]
@@ -524,7 +555,8 @@ def main():
                   "speedup_vs_fp64": (fp64["ms"] / mixed_ms) if fp64 else None},
         "roofline": {"kernel": "fused hop + M5^-1 (HOP_OE_M5INV, %s)" % args.sloppy, "bound": "hbm",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "bytes_per_launch": kbytes, "ms_per_launch": kms},
+                     "frac": achieved / peak, "traffic": stored_traffic("%s/HOP_OE_M5INV/%s" % (wl, args.sloppy)),
+                     "bytes_per_launch": kbytes, "ms_per_launch": kms},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "GB/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(b4h.numel() * 16), "d2h_bytes_per_step": int(qh.numel() * 16)},

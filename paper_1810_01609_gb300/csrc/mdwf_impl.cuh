@@ -299,14 +299,14 @@ __device__ __forceinline__ void chain_col(const SChain& ch, bool lower, C* col, 
   for (int s = 0; s < L; s++) col[s * st] = y[s];
 }
 
-// chain on one strided column in shared memory: unrolled register code for Ls <= 16
+// chain on one strided column in shared memory: unrolled register code for the common
+// Ls = 8, 10, 12, 16 (few variants keep the kernels' code small), a loop otherwise
 template <typename C>
 __device__ __forceinline__ void chain_apply_fast(const SChain& ch, int comp, C* col, int st, int Ls, C mf) {
   const bool lower = ((comp >> 1) & 3) >= 2;
   switch (Ls) {
 #define CASE_L(L) case L: chain_col<C, L>(ch, lower, col, st, mf); return;
-    CASE_L(2) CASE_L(3) CASE_L(4) CASE_L(5) CASE_L(6) CASE_L(7) CASE_L(8) CASE_L(9)
-    CASE_L(10) CASE_L(11) CASE_L(12) CASE_L(13) CASE_L(14) CASE_L(15) CASE_L(16)
+    CASE_L(8) CASE_L(10) CASE_L(12) CASE_L(16)
 #undef CASE_L
     default: chain_apply(ch, comp, col, st, Ls, mf);
   }
