@@ -1,0 +1,347 @@
+// Wilson hopping term of the Moebius domain-wall operator (Sec. "Current State of the
+// Art": a radius-one stencil on L^3 x T x L5 x Nc x Ns), fused with the s-direction
+// operators (M5 / M5^-1 / D5), the CG axpy and FP64-accumulated norms.
+//
+//   H psi(x) = sum_mu (1 - sig gamma_mu) U_mu(x) psi(x+mu) + (1 + sig gamma_mu) U_mu(x-mu)^+ psi(x-mu)
+//   sig = +1 for H, -1 for H^+ = gamma5 H gamma5.
+//
+// Chiral basis gamma_mu = [[0, X_mu], [X_mu^+, 0]], X_k = i sigma_k, X_t = 1:
+// (1 - sig gamma_mu) psi = (h, -sig X_mu^+ h) with the half spinor h = psi_u - sig X_mu psi_d,
+// so each direction multiplies one SU(3) matrix into two colour vectors.
+//
+// Thread layout: a CTA owns ns whole 4D sites; thread (site_l, r, s) computes the hop of
+// one 5D site of one right-hand side, so link loads are shared by the nrhs * Ls threads of
+// a site through L1.  The epilogue stages the hop result in shared memory, where one
+// thread per (site, rhs, real component) applies the s-direction chains in place.
+#pragma once
+#include "mdwf_impl.cuh"
+#include "mdwf_kernels.h"
+#include "mdwf_epi.cuh"
+#include <type_traits>
+
+namespace mdwf {
+
+template <typename C>
+struct cplx { C re, im; };
+
+// psi[24] ordered [colour][spin][re,im]
+#define PRE(sp, co) psi[2 * ((co) * 4 + (sp))]
+#define PIM(sp, co) psi[2 * ((co) * 4 + (sp)) + 1]
+#define ARE(sp, co) acc[2 * ((co) * 4 + (sp))]
+#define AIM(sp, co) acc[2 * ((co) * 4 + (sp)) + 1]
+
+template <int MU, int SIG, typename C>
+__device__ __forceinline__ void hop_dir(const C psi[24], const C U[18], C acc[24]) {
+  const C sg = (C)SIG;
+  cplx<C> h0[3], h1[3];
+#pragma unroll
+  for (int co = 0; co < 3; co++) {
+    if (MU == 0) {         // h0 = p0 - s i p3 ; h1 = p1 - s i p2
+      h0[co] = {PRE(0, co) + sg * PIM(3, co), PIM(0, co) - sg * PRE(3, co)};
+      h1[co] = {PRE(1, co) + sg * PIM(2, co), PIM(1, co) - sg * PRE(2, co)};
+    } else if (MU == 1) {  // h0 = p0 - s p3 ; h1 = p1 + s p2
+      h0[co] = {PRE(0, co) - sg * PRE(3, co), PIM(0, co) - sg * PIM(3, co)};
+      h1[co] = {PRE(1, co) + sg * PRE(2, co), PIM(1, co) + sg * PIM(2, co)};
+    } else if (MU == 2) {  // h0 = p0 - s i p2 ; h1 = p1 + s i p3
+      h0[co] = {PRE(0, co) + sg * PIM(2, co), PIM(0, co) - sg * PRE(2, co)};
+      h1[co] = {PRE(1, co) - sg * PIM(3, co), PIM(1, co) + sg * PRE(3, co)};
+    } else {               // h0 = p0 - s p2 ; h1 = p1 - s p3
+      h0[co] = {PRE(0, co) - sg * PRE(2, co), PIM(0, co) - sg * PIM(2, co)};
+      h1[co] = {PRE(1, co) - sg * PRE(3, co), PIM(1, co) - sg * PIM(3, co)};
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    cplx<C> u0 = {0, 0}, u1 = {0, 0};
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+      const C ur = U[2 * (3 * a + b)], ui = U[2 * (3 * a + b) + 1];
+      u0.re += ur * h0[b].re - ui * h0[b].im;
+      u0.im += ur * h0[b].im + ui * h0[b].re;
+      u1.re += ur * h1[b].re - ui * h1[b].im;
+      u1.im += ur * h1[b].im + ui * h1[b].re;
+    }
+    ARE(0, a) += u0.re; AIM(0, a) += u0.im;
+    ARE(1, a) += u1.re; AIM(1, a) += u1.im;
+    if (MU == 0) {         // lower0 = s i Uh1 ; lower1 = s i Uh0
+      ARE(2, a) -= sg * u1.im; AIM(2, a) += sg * u1.re;
+      ARE(3, a) -= sg * u0.im; AIM(3, a) += sg * u0.re;
+    } else if (MU == 1) {  // lower0 = s Uh1 ; lower1 = -s Uh0
+      ARE(2, a) += sg * u1.re; AIM(2, a) += sg * u1.im;
+      ARE(3, a) -= sg * u0.re; AIM(3, a) -= sg * u0.im;
+    } else if (MU == 2) {  // lower0 = s i Uh0 ; lower1 = -s i Uh1
+      ARE(2, a) -= sg * u0.im; AIM(2, a) += sg * u0.re;
+      ARE(3, a) += sg * u1.im; AIM(3, a) -= sg * u1.re;
+    } else {               // lower0 = -s Uh0 ; lower1 = -s Uh1
+      ARE(2, a) -= sg * u0.re; AIM(2, a) -= sg * u0.im;
+      ARE(3, a) -= sg * u1.re; AIM(3, a) -= sg * u1.im;
+    }
+  }
+}
+
+// Load one link (18 reals, row-major [a][b] complex) in compute precision.
+template <int P, bool R12>
+__device__ __forceinline__ void load_link(const void* base, long long off, typename PT<P>::C U[18],
+                                          bool flip) {
+  using C = typename PT<P>::C;
+  constexpr int NR = R12 ? 12 : 18;
+  if constexpr (P == F64) {
+    const double2* g = (const double2*)((const double*)base + off);
+#pragma unroll
+    for (int i = 0; i < NR / 2; i++) { double2 q = __ldg(g + i); U[2 * i] = q.x; U[2 * i + 1] = q.y; }
+  } else if constexpr (P == F32) {
+    const float4* g = (const float4*)((const float*)base + off);
+    constexpr int NQ = R12 ? 3 : 5;
+    float t[20];
+#pragma unroll
+    for (int i = 0; i < NQ; i++) { float4 q = __ldg(g + i); t[4 * i] = q.x; t[4 * i + 1] = q.y; t[4 * i + 2] = q.z; t[4 * i + 3] = q.w; }
+#pragma unroll
+    for (int i = 0; i < NR; i++) U[i] = t[i];
+  } else {
+    using G = typename PT<P>::G;
+    const uint4* g = (const uint4*)((const G*)base + off);
+    constexpr int NQ = R12 ? 2 : 3;
+    uint32_t t[12];
+#pragma unroll
+    for (int i = 0; i < NQ; i++) { uint4 q = __ldg(g + i); t[4 * i] = q.x; t[4 * i + 1] = q.y; t[4 * i + 2] = q.z; t[4 * i + 3] = q.w; }
+#pragma unroll
+    for (int i = 0; i < NR / 2; i++) {
+      float2 f;
+      if constexpr (P == F16) f = __half22float2(*(const __half2*)&t[i]);
+      else f = __bfloat1622float2(*(const __nv_bfloat162*)&t[i]);
+      U[2 * i] = f.x; U[2 * i + 1] = f.y;
+    }
+  }
+  if constexpr (R12) {
+    // row2 = conj(row0 x row1), times the boundary phase the stored rows carry
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      const int i = (k + 1) % 3, j = (k + 2) % 3;
+      const C ar = U[2 * i], ai = U[2 * i + 1], br = U[6 + 2 * j], bi = U[6 + 2 * j + 1];
+      const C cr = U[2 * j], ci = U[2 * j + 1], dr = U[6 + 2 * i], di = U[6 + 2 * i + 1];
+      C re = (ar * br - ai * bi) - (cr * dr - ci * di);
+      C im = (ar * bi + ai * br) - (cr * di + ci * dr);
+      U[12 + 2 * k] = flip ? -re : re;
+      U[12 + 2 * k + 1] = flip ? im : -im;
+    }
+  }
+}
+
+// SU(3) on a projected half spinor h (2 slots x 3 colours, complex) and reconstruction:
+// upper spins += U h, lower spins += -sig X_mu^+ U h.
+template <int MU, int SIG, typename C>
+__device__ __forceinline__ void su3_recon(const C h[12], const C* U, C acc[24]) {
+  const C sg = (C)SIG;
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    cplx<C> u0, u1;
+    {
+      const C ur = U[6 * a], ui = U[6 * a + 1];
+      u0.re = ur * h[0] - ui * h[1]; u0.im = ur * h[1] + ui * h[0];
+      u1.re = ur * h[6] - ui * h[7]; u1.im = ur * h[7] + ui * h[6];
+    }
+#pragma unroll
+    for (int b = 1; b < 3; b++) {
+      const C ur = U[2 * (3 * a + b)], ui = U[2 * (3 * a + b) + 1];
+      u0.re += ur * h[2 * b] - ui * h[2 * b + 1];
+      u0.im += ur * h[2 * b + 1] + ui * h[2 * b];
+      u1.re += ur * h[6 + 2 * b] - ui * h[6 + 2 * b + 1];
+      u1.im += ur * h[6 + 2 * b + 1] + ui * h[6 + 2 * b];
+    }
+    ARE(0, a) += u0.re; AIM(0, a) += u0.im;
+    ARE(1, a) += u1.re; AIM(1, a) += u1.im;
+    if (MU == 0) {         // lower0 = s i Uh1 ; lower1 = s i Uh0
+      ARE(2, a) -= sg * u1.im; AIM(2, a) += sg * u1.re;
+      ARE(3, a) -= sg * u0.im; AIM(3, a) += sg * u0.re;
+    } else if (MU == 1) {  // lower0 = s Uh1 ; lower1 = -s Uh0
+      ARE(2, a) += sg * u1.re; AIM(2, a) += sg * u1.im;
+      ARE(3, a) -= sg * u0.re; AIM(3, a) -= sg * u0.im;
+    } else if (MU == 2) {  // lower0 = s i Uh0 ; lower1 = -s i Uh1
+      ARE(2, a) -= sg * u0.im; AIM(2, a) += sg * u0.re;
+      ARE(3, a) += sg * u1.im; AIM(3, a) -= sg * u1.re;
+    } else {               // lower0 = -s Uh0 ; lower1 = -s Uh1
+      ARE(2, a) -= sg * u0.re; AIM(2, a) -= sg * u0.im;
+      ARE(3, a) -= sg * u1.re; AIM(3, a) -= sg * u1.im;
+    }
+  }
+}
+
+template <int P>
+__device__ __forceinline__ auto mk2(float a, float b) {
+  if constexpr (P == F16) return __floats2half2_rn(a, b);
+  else return __floats2bfloat162_rn(a, b);
+}
+
+// Neighbour column -> projected half spinor h (slot j, colour c at h[6j + 2c]) in the
+// compute precision.  F16 / BF16 project in 16-bit pairs before converting (one rounding
+// of the pair sum, then exact conversion), then scale by the per-site norm.
+template <int P, int MU, int SIG>
+__device__ __forceinline__ void load_proj(const Field& f, unsigned nbr, int col, typename PT<P>::C h[12]) {
+  using C = typename PT<P>::C;
+  if constexpr (P == F64 || P == F32) {
+    C psi[24];
+    load_site<P>(f, nbr, col, psi);
+    const C sg = (C)SIG;
+#pragma unroll
+    for (int co = 0; co < 3; co++) {
+      C* h0 = h + 2 * co;
+      C* h1 = h + 6 + 2 * co;
+      if (MU == 0) {
+        h0[0] = PRE(0, co) + sg * PIM(3, co); h0[1] = PIM(0, co) - sg * PRE(3, co);
+        h1[0] = PRE(1, co) + sg * PIM(2, co); h1[1] = PIM(1, co) - sg * PRE(2, co);
+      } else if (MU == 1) {
+        h0[0] = PRE(0, co) - sg * PRE(3, co); h0[1] = PIM(0, co) - sg * PIM(3, co);
+        h1[0] = PRE(1, co) + sg * PRE(2, co); h1[1] = PIM(1, co) + sg * PIM(2, co);
+      } else if (MU == 2) {
+        h0[0] = PRE(0, co) + sg * PIM(2, co); h0[1] = PIM(0, co) - sg * PRE(2, co);
+        h1[0] = PRE(1, co) - sg * PIM(3, co); h1[1] = PIM(1, co) + sg * PRE(3, co);
+      } else {
+        h0[0] = PRE(0, co) - sg * PRE(2, co); h0[1] = PIM(0, co) - sg * PIM(2, co);
+        h1[0] = PRE(1, co) - sg * PRE(3, co); h1[1] = PIM(1, co) - sg * PIM(3, co);
+      }
+    }
+  } else {
+    using H2 = typename std::conditional<P == F16, __half2, __nv_bfloat162>::type;
+    const uint4* d = (const uint4*)f.data;
+    const unsigned W = (unsigned)f.W();
+    float nrm = 1.0f;
+    if constexpr (P == F16) nrm = __ldg(f.norm + nbr * W + col);
+    const H2 ps = mk2<P>((float)SIG, (float)SIG);
+#pragma unroll
+    for (int co = 0; co < 3; co++) {
+      const uint4 q = __ldg(d + (nbr * 3 + co) * W + col);
+      const H2 w0 = *(const H2*)&q.x, w1 = *(const H2*)&q.y, w2 = *(const H2*)&q.z, w3 = *(const H2*)&q.w;
+      H2 r0, r1;
+      if (MU == 0 || MU == 2) {
+        // i * w = (-w.im, w.re): h0 = w0 - s i wA, h1 = w1 -+ s i wB
+        const H2 iA = MU == 0 ? __lowhigh2highlow(w3) : __lowhigh2highlow(w2);
+        const H2 iB = MU == 0 ? __lowhigh2highlow(w2) : __lowhigh2highlow(w3);
+        // -s i wA = s (wA.im, -wA.re) = iA * (s, -s)
+        const H2 m0 = mk2<P>((float)SIG, (float)-SIG);
+        r0 = __hfma2(iA, m0, w0);
+        r1 = MU == 0 ? __hfma2(iB, m0, w1) : __hfma2(iB, __hneg2(m0), w1);
+      } else if (MU == 1) {
+        r0 = __hfma2(w3, __hneg2(ps), w0);
+        r1 = __hfma2(w2, ps, w1);
+      } else {
+        r0 = __hfma2(w2, __hneg2(ps), w0);
+        r1 = __hfma2(w3, __hneg2(ps), w1);
+      }
+      float2 f0, f1;
+      if constexpr (P == F16) { f0 = __half22float2(r0); f1 = __half22float2(r1); }
+      else { f0 = __bfloat1622float2(r0); f1 = __bfloat1622float2(r1); }
+      h[2 * co] = f0.x * nrm; h[2 * co + 1] = f0.y * nrm;
+      h[6 + 2 * co] = f1.x * nrm; h[6 + 2 * co + 1] = f1.y * nrm;
+    }
+  }
+}
+
+// Link staging stride in shared memory (compute-precision reals per link, 16-byte rows)
+template <typename C> __host__ __device__ constexpr int link_stride() { return sizeof(C) == 8 ? 18 : 20; }
+
+template <int P, bool DAG, bool R12, bool EPI>
+__global__ void __launch_bounds__(MAXTHREADS)
+hop_kernel(const __grid_constant__ HopParams p) {
+  using C = typename PT<P>::C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Ls = p.in.Ls, nrhs = p.in.nrhs;
+  const int W = Ls * nrhs;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int site_l = tid / W;
+  const int col = tid - site_l * W;
+  const long long site0 = (long long)blockIdx.x * p.ns;
+  const long long x_cb = site0 + site_l;
+  const bool active = x_cb < p.g.vh;
+  constexpr int SF = DAG ? -1 : 1;
+  constexpr int LSTR = link_stride<C>();
+  // shared: links of the CTA's sites (compute precision), neighbour table, epilogue
+  C* slink = (C*)smem_raw;
+  unsigned* snbr = (unsigned*)(slink + p.ns * 8 * LSTR);
+  unsigned char* epi_base = (unsigned char*)(snbr + ((p.ns * 8 + 3) & ~3));
+
+  // phase 0: one thread per (site, direction) loads and converts the link, and finds the
+  // neighbour; forward links carry the boundary phase on t at T-1, backward ones on t at 0
+  for (int i = tid; i < p.ns * 8; i += nt) {
+    const long long x = site0 + (i >> 3);
+    if (x >= p.g.vh) continue;
+    const int d = i & 7, mu = d & 3;
+    int c[4];
+    cb_coords(p.g, x, p.pout, c);
+    snbr[i] = (unsigned)nbr_cb(p.g, c, mu, d < 4 ? +1 : -1);
+    C U[18];
+    const bool flip = R12 && mu == 3 && p.t_bc < 0 && (d < 4 ? c[3] == p.g.T - 1 : c[3] == 0);
+    load_link<P, R12>(p.gauge, (x * 8 + d) * p.gs, U, flip);
+#pragma unroll
+    for (int k = 0; k < 18; k++) slink[i * LSTR + k] = U[k];
+  }
+  __syncthreads();
+
+  C acc[24];
+#pragma unroll
+  for (int i = 0; i < 24; i++) acc[i] = 0;
+  if (active) {
+    const unsigned* nb = snbr + site_l * 8;
+    const C* lk = slink + site_l * 8 * LSTR;
+    C h[12];
+#define HOP_D(D, MU, SIG)                                   \
+    load_proj<P, MU, SIG>(p.in, nb[D], col, h);             \
+    su3_recon<MU, SIG>(h, lk + (D) * LSTR, acc);
+    HOP_D(0, 0, SF) HOP_D(4, 0, -SF) HOP_D(1, 1, SF) HOP_D(5, 1, -SF)
+    HOP_D(2, 2, SF) HOP_D(6, 2, -SF) HOP_D(3, 3, SF) HOP_D(7, 3, -SF)
+#undef HOP_D
+  }
+
+  if constexpr (!EPI) {
+    if (active) store_site<P>(p.out, x_cb, col, acc);
+    return;
+  } else {
+    const int GS = tile_gstr(Ls);
+    const int ngrp = p.ns * nrhs;
+    C* tileH = (C*)epi_base;
+    C* tileC = tileH + ngrp * GS;
+    const size_t toff = ((size_t)ngrp * GS * sizeof(C) * (p.has_center ? 2 : 1) + 15) & ~(size_t)15;
+    double* redsm = (double*)(epi_base + toff);
+    const int r = col / Ls, s = col - r * Ls;
+    const int grp = site_l * nrhs + r;
+    if (active) {
+      C* dst = tileH + grp * GS + s * TSTR;
+      if constexpr (sizeof(C) == 4) {
+#pragma unroll
+        for (int k = 0; k < 24; k += 4) *(float4*)(dst + k) = make_float4(acc[k], acc[k + 1], acc[k + 2], acc[k + 3]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 24; k += 2) *(double2*)(dst + k) = make_double2(acc[k], acc[k + 1]);
+      }
+    }
+    __syncthreads();
+    hop_epilogue<P>(p, tileH, tileC, redsm, p.ns);
+  }
+}
+
+template <int P, bool DAG, bool R12, bool EPI>
+static cudaError_t launch_one(const HopParams& p, int threads, size_t smem, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(hop_kernel<P, DAG, R12, EPI>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const long long blocks = (p.g.vh + p.ns - 1) / p.ns;
+  hop_kernel<P, DAG, R12, EPI><<<(unsigned)blocks, threads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+// all (dagger, 12-real links, epilogue) variants of one storage precision
+template <int P>
+cudaError_t launch_hop_prec(const HopParams& p, bool dag, bool r12, bool epi, int threads, size_t smem,
+                            cudaStream_t st) {
+  if (dag) {
+    if (r12) return epi ? launch_one<P, true, true, true>(p, threads, smem, st) : launch_one<P, true, true, false>(p, threads, smem, st);
+    return epi ? launch_one<P, true, false, true>(p, threads, smem, st) : launch_one<P, true, false, false>(p, threads, smem, st);
+  }
+  if (r12) return epi ? launch_one<P, false, true, true>(p, threads, smem, st) : launch_one<P, false, true, false>(p, threads, smem, st);
+  return epi ? launch_one<P, false, false, true>(p, threads, smem, st) : launch_one<P, false, false, false>(p, threads, smem, st);
+}
+
+}  // namespace mdwf
