@@ -130,8 +130,8 @@ __device__ __forceinline__ void load_link(const void* base, long long off, typen
 // SU(3) on a projected half spinor h (2 slots x 3 colours, complex) and reconstruction:
 // upper spins += U h, lower spins += -sig X_mu^+ U h.
 template <int MU, int SIG, typename C>
-__device__ __forceinline__ void su3_recon(const C h[12], const C* U, C acc[24]) {
-  const C sg = (C)SIG;
+__device__ __forceinline__ void su3_recon(const C h[12], const C* U, C acc[24], const C n) {
+  const C sg = (C)SIG * n;   // the neighbour's storage scale folds into the accumulation
 #pragma unroll
   for (int a = 0; a < 3; a++) {
     cplx<C> u0, u1;
@@ -148,8 +148,8 @@ __device__ __forceinline__ void su3_recon(const C h[12], const C* U, C acc[24]) 
       u1.re += ur * h[6 + 2 * b] - ui * h[6 + 2 * b + 1];
       u1.im += ur * h[6 + 2 * b + 1] + ui * h[6 + 2 * b];
     }
-    ARE(0, a) += u0.re; AIM(0, a) += u0.im;
-    ARE(1, a) += u1.re; AIM(1, a) += u1.im;
+    ARE(0, a) += n * u0.re; AIM(0, a) += n * u0.im;
+    ARE(1, a) += n * u1.re; AIM(1, a) += n * u1.im;
     if (MU == 0) {         // lower0 = s i Uh1 ; lower1 = s i Uh0
       ARE(2, a) -= sg * u1.im; AIM(2, a) += sg * u1.re;
       ARE(3, a) -= sg * u0.im; AIM(3, a) += sg * u0.re;
@@ -176,7 +176,7 @@ __device__ __forceinline__ auto mk2(float a, float b) {
 // compute precision.  F16 / BF16 project in 16-bit pairs before converting (one rounding
 // of the pair sum, then exact conversion), then scale by the per-site norm.
 template <int P, int MU, int SIG>
-__device__ __forceinline__ void load_proj(const Field& f, unsigned nbr, int col, typename PT<P>::C h[12]) {
+__device__ __forceinline__ typename PT<P>::C load_proj(const Field& f, unsigned nbr, int col, typename PT<P>::C h[12]) {
   using C = typename PT<P>::C;
   if constexpr (P == F64 || P == F32) {
     C psi[24];
@@ -200,6 +200,7 @@ __device__ __forceinline__ void load_proj(const Field& f, unsigned nbr, int col,
         h1[0] = PRE(1, co) - sg * PRE(3, co); h1[1] = PIM(1, co) - sg * PIM(3, co);
       }
     }
+    return (C)1;
   } else {
     using H2 = typename std::conditional<P == F16, __half2, __nv_bfloat162>::type;
     const uint4* d = (const uint4*)f.data;
@@ -230,9 +231,10 @@ __device__ __forceinline__ void load_proj(const Field& f, unsigned nbr, int col,
       float2 f0, f1;
       if constexpr (P == F16) { f0 = __half22float2(r0); f1 = __half22float2(r1); }
       else { f0 = __bfloat1622float2(r0); f1 = __bfloat1622float2(r1); }
-      h[2 * co] = f0.x * nrm; h[2 * co + 1] = f0.y * nrm;
-      h[6 + 2 * co] = f1.x * nrm; h[6 + 2 * co + 1] = f1.y * nrm;
+      h[2 * co] = f0.x; h[2 * co + 1] = f0.y;
+      h[6 + 2 * co] = f1.x; h[6 + 2 * co + 1] = f1.y;
     }
+    return nrm;
   }
 }
 
@@ -283,9 +285,9 @@ hop_kernel(const __grid_constant__ HopParams p) {
     const unsigned* nb = snbr + site_l * 8;
     const C* lk = slink + site_l * 8 * LSTR;
     C h[12];
-#define HOP_D(D, MU, SIG)                                   \
-    load_proj<P, MU, SIG>(p.in, nb[D], col, h);             \
-    su3_recon<MU, SIG>(h, lk + (D) * LSTR, acc);
+#define HOP_D(D, MU, SIG)                                                 \
+    { const C nrm = load_proj<P, MU, SIG>(p.in, nb[D], col, h);           \
+      su3_recon<MU, SIG>(h, lk + (D) * LSTR, acc, nrm); }
     HOP_D(0, 0, SF) HOP_D(4, 0, -SF) HOP_D(1, 1, SF) HOP_D(5, 1, -SF)
     HOP_D(2, 2, SF) HOP_D(6, 2, -SF) HOP_D(3, 3, SF) HOP_D(7, 3, -SF)
 #undef HOP_D
