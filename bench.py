@@ -541,7 +541,7 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f16+f32 (inner), f64 (reliable updates, reductions)",
+        "vs_baseline": None, "dtype": "f32 arithmetic on f16 storage (inner CG); f64 reliable updates and reductions",
         "data": "synthetic",
         "config": {"workload": wl, "lattice": list(dims), "Ls": Ls, "mf": mf, "b5": 1.5, "c5": 0.5, "M5": 1.3,
                    "link_eps": eps, "seed": seed, "source": "point (spin 0, colour 0, origin)",

@@ -87,3 +87,36 @@ def test_zero_source_and_bad_args():
     x, info = ctx.solve(b, maxiter=5, check_interval=5)
     assert info.status == m.MDWF_ERR_NOT_CONVERGED and info.iterations == 5
     assert np.any(x)
+
+
+@pytest.mark.parametrize("b5,c5,M5,recon", [(1.0, 0.0, 1.8, 18), (2.0, 1.0, 1.2, 12), (1.5, 0.5, 1.3, 12)])
+def test_solve_other_parameters(b5, c5, M5, recon):
+    """Shamir-type kernel (c5 = 0), other Moebius scales and heights, and 12-real link
+    storage: mixed solve vs the oracle solve with the same parameters."""
+    m = lib()
+    dims, Ls, mf = (4, 4, 2, 4), 6, 0.04
+    U = inputs.gauge_links(dims, 0.3, 13)
+    p = MobiusParams(Ls=Ls, b5=b5, c5=c5, M5=M5, mf=mf)
+    Ub = dirac.boundary_links(U, -1.0)
+    b = inputs.gaussian_spinor5d(dims, Ls, 14)
+    xo, _, _ = solve.solve_eo(Ub, b, p, tol=1e-12)
+    ctx = m.Context(dims, Ls, b5=b5, c5=c5, M5=M5, mf=mf, recon=recon)
+    ctx.load_gauge(U)
+    x, info = ctx.solve(to_dev(b), tol=1e-10, sloppy="f16")
+    assert info.true_residual <= 1e-10
+    assert rel(to_host(x), xo) <= 1e-8
+
+
+def test_periodic_time_boundary():
+    m = lib()
+    dims, Ls, mf = (4, 4, 4, 4), 4, 0.1
+    U = inputs.gauge_links(dims, 0.3, 15)
+    p = MobiusParams(Ls=Ls, mf=mf, t_bc=1.0)
+    Ub = dirac.boundary_links(U, 1.0)
+    b = inputs.gaussian_spinor5d(dims, Ls, 16)
+    xo, _, _ = solve.solve_eo(Ub, b, p, tol=1e-12)
+    ctx = m.Context(dims, Ls, mf=mf, t_bc=1.0)
+    ctx.load_gauge(U)
+    x, info = ctx.solve(b, tol=1e-10, sloppy="bf16")
+    assert info.true_residual <= 1e-10
+    assert rel(x, xo) <= 1e-8
