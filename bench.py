@@ -319,6 +319,7 @@ def mode_large48(args):
                       "mf": mf, "link_eps": eps, "seed": seed, "links": "device Philox (inputs.gauge_links_device)",
                       "sloppy": args.sloppy, "tol": 1e-10},
            "solve": {"ms": ms, "iterations": info.iterations, "reliable_updates": info.reliable_updates,
+                     "fp64_residuals": info.fp64_residuals,
                      "true_residual": info.true_residual, "full_residual": info.full_residual},
            "device_memory_peak_gb": torch.cuda.max_memory_allocated() / 1e9}
     print(json.dumps(out))
@@ -549,7 +550,8 @@ def main():
                    "l2": "step working set > L2; roofline kernel launches preceded by a 512 MB L2 flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "solve": {"mixed_ms": mixed_ms, "iterations": infos[-1].iterations,
-                  "reliable_updates": infos[-1].reliable_updates, "true_residual": infos[-1].true_residual,
+                  "reliable_updates": infos[-1].reliable_updates, "fp64_residuals": infos[-1].fp64_residuals,
+                  "true_residual": infos[-1].true_residual,
                   "full_residual": infos[-1].full_residual,
                   "fp64_ms": fp64["ms"] if fp64 else None, "fp64_iterations": fp64["iterations"] if fp64 else None,
                   "fp64_true_residual": fp64["true_residual"] if fp64 else None,

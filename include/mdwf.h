@@ -125,10 +125,13 @@ typedef struct mdwf_solve_params {
 typedef struct mdwf_solve_info {
   int status;              /* MDWF_SUCCESS or MDWF_ERR_NOT_CONVERGED / _BREAKDOWN */
   int iterations;          /* inner CG iterations */
-  int reliable_updates;    /* FP64 residual recomputations (mixed precision) */
+  int reliable_updates;    /* reliable updates (mixed precision): x64 += x_s and the inner
+                              residual restarted from res = b~ - M x64 */
   double true_residual;    /* FP64 |b~ - M_pc x| / |b~| of the preconditioned system */
   double full_residual;    /* FP64 |b - D x| / |b| (if requested, else -1) */
   double time_ms;          /* wall time of the call (host clock, stream synchronised) */
+  int fp64_residuals;      /* residuals b~ - M_pc x recomputed with M_pc in FP64 (the others
+                              are updated as res -= M_pc x_s with M_pc in FP32) */
 } mdwf_solve_info;
 
 typedef struct mdwf_ctx mdwf_ctx;

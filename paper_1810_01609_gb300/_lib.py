@@ -45,7 +45,7 @@ class mdwf_solve_params(ctypes.Structure):
 class mdwf_solve_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("reliable_updates", ctypes.c_int),
                 ("true_residual", ctypes.c_double), ("full_residual", ctypes.c_double),
-                ("time_ms", ctypes.c_double)]
+                ("time_ms", ctypes.c_double), ("fp64_residuals", ctypes.c_int)]
 
 
 class MdwfError(RuntimeError):

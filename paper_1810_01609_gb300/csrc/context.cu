@@ -717,6 +717,7 @@ struct SolveState {
   std::vector<int> done;
   std::vector<int> iters;
   int ru = 0;
+  int fp64_res = 0;               // FP64 recomputations of b~ - M x
 };
 
 // res = b~ - M_pc x (FP64), |res|^2 per rhs
@@ -797,6 +798,7 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
 
   const int interval = std::max(1, sp->check_interval);
   int ru_since_anchor = 0;
+  bool x_fresh = false;   // res holds the FP64 residual of the current x (no iterations since)
   int it = 0;
   bool first = true;
   int status = MDWF_SUCCESS;
@@ -810,6 +812,7 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
     // before any capture
     CKS(run_iterations(c, v, n, sp->use_graph && !first && n == interval, st));
     first = false;
+    x_fresh = false;
     it += n;
     CKS(pull_scalars(c, nrhs, st));
     bool need_true = false, need_ru = false;
@@ -831,17 +834,14 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
     if (mixed) {
       // Reliable update.  An FP64 anchor recomputes res = b~ - M x64 in FP64; in between,
       // res -= M x_s with M applied in FP32 to the inner accumulator (its rounding error is
-      // ~1e-7 of that correction, itself ~delta of the residual), then x64 += x_s.
+      // ~1e-7 |M| |x_s|, x_s being the correction since the last update), then x64 += x_s.
+      // Every third update is an anchor, and so is any update whose incremental residual
+      // says the tolerance is reached or the inner normal residual hit its stopping value:
+      // convergence is only declared on an FP64 residual.
       S->ru++;
-      double worst = 0.0;
-      for (int r = 0; r < nrhs; r++)
-        if (!S->done[r]) worst = std::max(worst, S->true_rel[r]);
-      anchor = need_true || ru_since_anchor >= 2 || worst <= 1e4 * sp->tol;
-      if (anchor) {
-        CKS(sl_convert(c, F64, x64, F32, v.x, true, true, st));
-        CKS(true_residual(c, bt, x64, res, rr2, st));
-        ru_since_anchor = 0;
-      } else {
+      anchor = need_true || ru_since_anchor >= 2;
+      bool folded = false;   // x_s already added to x64 in this update
+      if (!anchor) {
         Field q32, q64;
         CKS(ws_half(c, "ru_q32", F32, nrhs, &q32));
         CKS(ws_half(c, "tr_q", F64, nrhs, &q64));
@@ -852,10 +852,22 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
         CK(cudaStreamSynchronize(st));
         rr2.assign(c->red_host, c->red_host + nrhs);
         CKS(sl_convert(c, F64, x64, F32, v.x, true, true, st));
+        folded = true;
         ru_since_anchor++;
+        for (int r = 0; r < nrhs; r++)
+          if (!S->done[r] && rr2[r] <= sp->tol * sp->tol * S->bnorm2[r]) anchor = true;
+      }
+      if (anchor) {
+        if (!folded) CKS(sl_convert(c, F64, x64, F32, v.x, true, true, st));
+        CKS(true_residual(c, bt, x64, res, rr2, st));
+        S->fp64_res++;
+        ru_since_anchor = 0;
+        x_fresh = true;
       }
     } else {
       CKS(true_residual(c, bt, v.x, res, rr2, st));
+      S->fp64_res++;
+      x_fresh = true;
     }
     for (int r = 0; r < nrhs; r++) {
       if (S->done[r]) continue;
@@ -872,6 +884,9 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
         s.hit = 0;
       }
     }
+    bool finished = true;
+    for (int r = 0; r < nrhs; r++) finished &= (bool)S->done[r];
+    if (finished) break;
     if (mixed) {
       // r = M^+ (b~ - M x) with the FP64 residual rounded to FP32 (relative precision of
       // the inner iteration is all it needs), requantised to the inner storage
@@ -898,13 +913,16 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
     }
     CKS(push_scalars(c, nrhs, st));
   }
-  if (mixed) CKS(sl_convert(c, F64, x64, F32, v.x, true, true, st));
-  else CK(cudaMemcpyAsync(x64.data, v.x.data, field_bytes_of(x64, F64), cudaMemcpyDeviceToDevice, st));
+  if (!mixed) CK(cudaMemcpyAsync(x64.data, v.x.data, field_bytes_of(x64, F64), cudaMemcpyDeviceToDevice, st));
   for (int r = 0; r < nrhs; r++) S->iters[r] = S->iters[r] ? S->iters[r] : it;
-  // final FP64 true residual
-  std::vector<double> rr2;
-  CKS(true_residual(c, bt, x64, res, rr2, st));
-  for (int r = 0; r < nrhs; r++) S->true_rel[r] = S->bnorm2[r] > 0 ? std::sqrt(rr2[r] / S->bnorm2[r]) : 0.0;
+  // final FP64 true residual, unless the last check already computed it for this x
+  if (!x_fresh) {
+    if (mixed) CKS(sl_convert(c, F64, x64, F32, v.x, true, true, st));
+    std::vector<double> rr2;
+    CKS(true_residual(c, bt, x64, res, rr2, st));
+    S->fp64_res++;
+    for (int r = 0; r < nrhs; r++) S->true_rel[r] = S->bnorm2[r] > 0 ? std::sqrt(rr2[r] / S->bnorm2[r]) : 0.0;
+  }
   return status;
 }
 
@@ -1231,6 +1249,7 @@ int mdwf_solve_multi(mdwf_ctx* c, int nrhs, const double* src, double* sol, cons
   for (int r = 0; r < nrhs; r++) {
     info[r].iterations = S.iters[r];
     info[r].reliable_updates = S.ru;
+    info[r].fp64_residuals = S.fp64_res;
     info[r].true_residual = S.true_rel[r];
     info[r].full_residual = full_rel[r];
     info[r].time_ms = ms;

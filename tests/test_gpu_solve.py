@@ -38,6 +38,11 @@ def test_solve_matches_oracle(sloppy, use_graph):
     assert rel(x, xo) <= 1e-8
     if sloppy != "f64":
         assert info.reliable_updates >= 1
+        # convergence is declared on an FP64 residual; between anchors the residual is
+        # updated incrementally, so there are fewer FP64 recomputations than updates + 1
+        assert 1 <= info.fp64_residuals <= info.reliable_updates + 1
+    else:
+        assert info.fp64_residuals >= 1
 
 
 def test_solve_host_buffers_and_ragged_lattice():

@@ -57,3 +57,27 @@ def test_host_side_argument_validation():
     except m.MdwfError as e:
         assert e.code == m.MDWF_ERR_ARG
     m.mdwf_destroy(ctx)
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors of the header's structs have the C compiler's sizes and offsets."""
+    import subprocess
+    import paper_1810_01609_gb300._lib as L
+    structs = {"mdwf_params": L.mdwf_params, "mdwf_solve_params": L.mdwf_solve_params,
+               "mdwf_solve_info": L.mdwf_solve_info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mdwf.h"', "int main(void) {"]
+    for sname, cls in structs.items():
+        lines.append('  printf("%s %%zu\\n", sizeof(%s));' % (sname, sname))
+        for fname, _ in cls._fields_:
+            lines.append('  printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (sname, fname, sname, fname))
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                  check=True).stdout.splitlines())
+    for sname, cls in structs.items():
+        assert int(got[sname]) == ctypes.sizeof(cls), sname
+        for fname, _ in cls._fields_:
+            assert int(got["%s.%s" % (sname, fname)]) == getattr(cls, fname).offset, (sname, fname)
