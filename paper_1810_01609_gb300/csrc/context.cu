@@ -381,6 +381,11 @@ int hop(mdwf_ctx* c, int prec, bool dag, const Field& in, const Field& out, int 
   p.post = e.post; p.hc = e.hc;
   p.has_center = e.center.data != nullptr;
   p.center = e.center; p.cop = e.cop; p.cc = e.cc;
+  // the epilogue applies the centre's operator per site from s +- 1: one bidiagonal op at most
+  if (e.cop.op[1].kind != SOP_NONE || e.cop.op[0].kind == SOP_INV) {
+    g_last_error = "internal: centre operator must be empty or one bidiagonal op";
+    return MDWF_ERR_ARG;
+  }
   p.norm_pre = e.norm_pre; p.fin = e.fin;
   p.axpy_r = e.raxpy.data != nullptr;
   p.raxpy = e.raxpy;

@@ -300,8 +300,7 @@ hop_kernel(const __grid_constant__ HopParams p) {
     const int GS = tile_gstr(Ls);
     const int ngrp = p.ns * nrhs;
     C* tileH = (C*)epi_base;
-    C* tileC = tileH + ngrp * GS;
-    const size_t toff = ((size_t)ngrp * GS * sizeof(C) * (p.has_center ? 2 : 1) + 15) & ~(size_t)15;
+    const size_t toff = ((size_t)ngrp * GS * sizeof(C) + 15) & ~(size_t)15;
     double* redsm = (double*)(epi_base + toff);
     const int r = col / Ls, s = col - r * Ls;
     const int grp = site_l * nrhs + r;
@@ -316,7 +315,7 @@ hop_kernel(const __grid_constant__ HopParams p) {
       }
     }
     __syncthreads();
-    hop_epilogue<P>(p, tileH, tileC, redsm, p.ns);
+    hop_epilogue<P>(p, tileH, redsm, p.ns);
   }
 }
 

@@ -153,7 +153,8 @@ __host__ __device__ inline MmaSmem mma_smem(int ns, int nrhs, int Ls, bool cente
   m.nbr_off = m.ref_off + ((ns * W * 4 + 15) & ~(size_t)15);
   m.tile_off = m.nbr_off + ((size_t)ns * 8 * 4 + 15) / 16 * 16;
   const size_t tile = (size_t)ns * nrhs * tile_gstr(Ls) * 4;
-  m.red_off = m.tile_off + ((tile * (center ? 2 : 1) + 15) & ~(size_t)15);
+  (void)center;
+  m.red_off = m.tile_off + ((tile + 15) & ~(size_t)15);
   const size_t nsites = (size_t)ns * W;
   m.total = m.red_off + ((nsites > (size_t)threads ? nsites : (size_t)threads) + (size_t)ns * nrhs) * 8 + 16;
   return m;
@@ -170,7 +171,6 @@ __global__ void __launch_bounds__(256) hop_mma_kernel(const __grid_constant__ Ho
   float* ref = (float*)(smem_raw + L.ref_off);
   int* nbrs = (int*)(smem_raw + L.nbr_off);
   float* tileH = (float*)(smem_raw + L.tile_off);
-  float* tileC = tileH + ns * nrhs * GS;
   double* redsm = (double*)(smem_raw + L.red_off);
 
   // phase 0: neighbour table of the CTA's sites
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(256) hop_mma_kernel(const __grid_constant__ Ho
     }
   }
   __syncthreads();
-  hop_epilogue<P>(p, tileH, tileC, redsm, ns);
+  hop_epilogue<P>(p, tileH, redsm, ns);
 }
 
 bool hop_tc_supported(int prec, const HopParams& p, bool r12) {
