@@ -177,7 +177,9 @@ int mdwf_apply(mdwf_ctx* ctx, int op, int prec, const void* in, void* out, int n
 /* Solve D x = b for one 5D source: b~_o = A5^-1 (b_o + H_oe D5 A5^-1 b_e / 2), CG on
  * M_pc^+ M_pc to |b~ - M_pc x_o| <= tol |b~| (FP64-recomputed), then
  * x_e = A5^-1 (b_e + H_eo D5 x_o / 2).  src/sol are user 5D fields at sp->location.
- * Returns MDWF_SUCCESS, MDWF_ERR_NOT_CONVERGED (solution still written) or an error. */
+ * Returns MDWF_SUCCESS, MDWF_ERR_NOT_CONVERGED (solution still written) or an error.
+ * With env MDWF_VERBOSE=1 every reliable update / residual check prints one line on
+ * stderr (iteration, kind: FP64 recomputation or FP32 incremental update, residual). */
 int mdwf_solve(mdwf_ctx* ctx, const double* src, double* sol,
                const mdwf_solve_params* sp, mdwf_solve_info* info, void* stream);
 /* The same for nrhs sources in one batched solve (contiguous [nrhs][...] user fields);

@@ -738,6 +738,12 @@ int true_residual(mdwf_ctx* c, const Field& bt, const Field& x, const Field& res
   return MDWF_SUCCESS;
 }
 
+// MDWF_VERBOSE=1: one line per reliable update / residual check on stderr
+static bool verbose() {
+  static const int v = [] { const char* e = getenv("MDWF_VERBOSE"); return e && e[0] == '1' ? 1 : 0; }();
+  return v != 0;
+}
+
 // CG on M_pc^+ M_pc for the odd-parity system M_pc x = bt (nrhs at once).
 // prec == F64: plain FP64 CG; otherwise mixed precision with reliable updates.
 int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_params* sp, SolveState* S,
@@ -841,10 +847,12 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
       // res -= M x_s with M applied in FP32 to the inner accumulator (its rounding error is
       // ~1e-7 |M| |x_s|, x_s being the correction since the last update), then x64 += x_s.
       // Every third update is an anchor, and so is any update whose incremental residual
-      // says the tolerance is reached or the inner normal residual hit its stopping value:
-      // convergence is only declared on an FP64 residual.
+      // says the tolerance is reached: convergence is only declared on an FP64 residual.
+      // When the inner normal residual hits its stopping value first, the incremental
+      // residual (accurate to ~1e-7 cond(M) of the last anchor's) decides whether an
+      // FP64 check is due or the inner target is tightened.
       S->ru++;
-      anchor = need_true || ru_since_anchor >= 2;
+      anchor = ru_since_anchor >= 2;
       bool folded = false;   // x_s already added to x64 in this update
       if (!anchor) {
         Field q32, q64;
@@ -874,12 +882,16 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
       S->fp64_res++;
       x_fresh = true;
     }
+    if (verbose())
+      for (int r = 0; r < nrhs; r++)
+        if (!S->done[r])
+          fprintf(stderr, "[mdwf] it %d rhs %d update %d %s residual %.3e%s\n", it, r, S->ru,
+                  anchor ? "fp64" : "incr", std::sqrt(rr2[r] / S->bnorm2[r]), c->cg_host[r].hit ? " (inner stop)" : "");
     for (int r = 0; r < nrhs; r++) {
       if (S->done[r]) continue;
       S->true_rel[r] = std::sqrt(rr2[r] / S->bnorm2[r]);
       CGScalars& s = c->cg_host[r];
-      if (!anchor) continue;   // convergence is only declared on an FP64 residual
-      if (S->true_rel[r] <= sp->tol) {
+      if (anchor && S->true_rel[r] <= sp->tol) {   // convergence only on an FP64 residual
         S->done[r] = 1;
         s.active = 0;
       } else if (s.hit) {
