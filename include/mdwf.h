@@ -179,7 +179,8 @@ int mdwf_apply(mdwf_ctx* ctx, int op, int prec, const void* in, void* out, int n
  * x_e = A5^-1 (b_e + H_eo D5 x_o / 2).  src/sol are user 5D fields at sp->location.
  * Returns MDWF_SUCCESS, MDWF_ERR_NOT_CONVERGED (solution still written) or an error.
  * With env MDWF_VERBOSE=1 every reliable update / residual check prints one line on
- * stderr (iteration, kind: FP64 recomputation or FP32 incremental update, residual). */
+ * stderr (iteration, kind: FP64 recomputation or FP32 incremental update, residual);
+ * MDWF_VERBOSE=2 also recomputes the FP64 residual at incremental updates (diagnostic). */
 int mdwf_solve(mdwf_ctx* ctx, const double* src, double* sol,
                const mdwf_solve_params* sp, mdwf_solve_info* info, void* stream);
 /* The same for nrhs sources in one batched solve (contiguous [nrhs][...] user fields);

@@ -738,11 +738,13 @@ int true_residual(mdwf_ctx* c, const Field& bt, const Field& x, const Field& res
   return MDWF_SUCCESS;
 }
 
-// MDWF_VERBOSE=1: one line per reliable update / residual check on stderr
-static bool verbose() {
-  static const int v = [] { const char* e = getenv("MDWF_VERBOSE"); return e && e[0] == '1' ? 1 : 0; }();
-  return v != 0;
+// MDWF_VERBOSE=1: one line per reliable update / residual check on stderr; 2: also the FP64
+// residual at every incremental update (diagnostic: costs one FP64 M_pc per update)
+static int verbose_level() {
+  static const int v = [] { const char* e = getenv("MDWF_VERBOSE"); return e ? atoi(e) : 0; }();
+  return v;
 }
+static bool verbose() { return verbose_level() > 0; }
 
 // CG on M_pc^+ M_pc for the odd-parity system M_pc x = bt (nrhs at once).
 // prec == F64: plain FP64 CG; otherwise mixed precision with reliable updates.
@@ -809,6 +811,10 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
 
   const int interval = std::max(1, sp->check_interval);
   int ru_since_anchor = 0;
+  // |res|^2 at the last FP64 residual (x = 0 at the start: res = b~ exactly)
+  std::vector<double> anchor_r2 = S->bnorm2;
+  constexpr double kAnchorRatio = 1.6e5;   // 1 % / eps32 (6e-8)
+  constexpr int kMaxIncremental = 8;       // at most this many incremental updates in a row
   bool x_fresh = false;   // res holds the FP64 residual of the current x (no iterations since)
   int it = 0;
   bool first = true;
@@ -846,13 +852,16 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
       // Reliable update.  An FP64 anchor recomputes res = b~ - M x64 in FP64; in between,
       // res -= M x_s with M applied in FP32 to the inner accumulator (its rounding error is
       // ~1e-7 |M| |x_s|, x_s being the correction since the last update), then x64 += x_s.
-      // Every third update is an anchor, and so is any update whose incremental residual
-      // says the tolerance is reached: convergence is only declared on an FP64 residual.
-      // When the inner normal residual hits its stopping value first, the incremental
-      // residual (accurate to ~1e-7 cond(M) of the last anchor's) decides whether an
-      // FP64 check is due or the inner target is tightened.
+      // The FP32 evaluations of M x_s since the last anchor leave a rounding error of order
+      // eps32 |res at the anchor| in res, so an anchor is due once that could exceed 1 % of
+      // the current residual (|res_anchor| / |res| > kAnchorRatio), and whenever the
+      // incremental residual says the tolerance is reached: convergence is only declared
+      // on an FP64 residual.  (Measured: incremental and FP64 residuals agree to four
+      // digits up to a ratio of ~1e4.)  When the inner normal residual hits its stopping
+      // value, the incremental residual decides whether an FP64 check is due or the inner
+      // target is tightened.
       S->ru++;
-      anchor = ru_since_anchor >= 2;
+      anchor = ru_since_anchor >= kMaxIncremental;
       bool folded = false;   // x_s already added to x64 in this update
       if (!anchor) {
         Field q32, q64;
@@ -867,8 +876,11 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
         CKS(sl_convert(c, F64, x64, F32, v.x, true, true, st));
         folded = true;
         ru_since_anchor++;
-        for (int r = 0; r < nrhs; r++)
-          if (!S->done[r] && rr2[r] <= sp->tol * sp->tol * S->bnorm2[r]) anchor = true;
+        for (int r = 0; r < nrhs; r++) {
+          if (S->done[r]) continue;
+          if (rr2[r] <= sp->tol * sp->tol * S->bnorm2[r]) anchor = true;
+          if (anchor_r2[r] > kAnchorRatio * kAnchorRatio * rr2[r]) anchor = true;
+        }
       }
       if (anchor) {
         if (!folded) CKS(sl_convert(c, F64, x64, F32, v.x, true, true, st));
@@ -876,17 +888,28 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
         S->fp64_res++;
         ru_since_anchor = 0;
         x_fresh = true;
+        anchor_r2 = rr2;
       }
     } else {
       CKS(true_residual(c, bt, v.x, res, rr2, st));
       S->fp64_res++;
       x_fresh = true;
     }
-    if (verbose())
-      for (int r = 0; r < nrhs; r++)
-        if (!S->done[r])
-          fprintf(stderr, "[mdwf] it %d rhs %d update %d %s residual %.3e%s\n", it, r, S->ru,
-                  anchor ? "fp64" : "incr", std::sqrt(rr2[r] / S->bnorm2[r]), c->cg_host[r].hit ? " (inner stop)" : "");
+    if (verbose()) {
+      std::vector<double> chk;
+      if (mixed && !anchor && verbose_level() >= 2) {
+        Field rd;
+        CKS(ws_half(c, "res_dbg", F64, nrhs, &rd));
+        CKS(true_residual(c, bt, x64, rd, chk, st));
+      }
+      for (int r = 0; r < nrhs; r++) {
+        if (S->done[r]) continue;
+        fprintf(stderr, "[mdwf] it %d rhs %d update %d %s residual %.3e", it, r, S->ru, anchor ? "fp64" : "incr",
+                std::sqrt(rr2[r] / S->bnorm2[r]));
+        if (!chk.empty()) fprintf(stderr, " (fp64 %.3e)", std::sqrt(chk[r] / S->bnorm2[r]));
+        fprintf(stderr, "%s\n", c->cg_host[r].hit ? " (inner stop)" : "");
+      }
+    }
     for (int r = 0; r < nrhs; r++) {
       if (S->done[r]) continue;
       S->true_rel[r] = std::sqrt(rr2[r] / S->bnorm2[r]);
