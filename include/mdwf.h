@@ -232,7 +232,9 @@ const char* mdwf_noalloc_last_error(void);
  * precision and mode; MDWF_TUNE_CACHE names a JSON file it is loaded from and saved to. */
 int mdwf_set_tuning(mdwf_ctx* ctx, int enable);
 /* Number of tune-cache entries, and the tuned sites-per-CTA of entry i with its time (ms)
- * and key (copied into key[keylen]). */
+ * and key (copied into key[keylen]).  For the fused 32-bit hop kernels the tuner also
+ * chooses between two builds: 65536 is added to sites_per_cta when it picked the
+ * occupancy-bounded one (at most 64 registers per thread). */
 int mdwf_tune_entries(const mdwf_ctx* ctx, int* count);
 int mdwf_tune_entry(const mdwf_ctx* ctx, int i, char* key, int keylen, int* sites_per_cta,
                     double* ms);

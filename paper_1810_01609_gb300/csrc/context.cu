@@ -95,9 +95,15 @@ SOp sop_none() {
   memset(&o, 0, sizeof o);
   return o;
 }
+// FP32 copies of the coefficients for the 32-bit kernels
+static void sop_round(SOp& o) {
+  o.fa = (float)o.a; o.fb = (float)o.b; o.finv_a = (float)o.inv_a; o.fc0 = (float)o.c0;
+  for (int j = 0; j < MAXLS; j++) o.fw[j] = (float)o.w[j];
+}
 SOp sop_bidiag(double a, double b, bool dag) {
   SOp o = sop_none();
   o.kind = SOP_BIDIAG; o.dag = dag; o.a = a; o.b = b; o.inv_a = 1.0 / a;
+  sop_round(o);
   return o;
 }
 // (a + b S)^-1 with S^Ls = -mf: x_{last} = c0 y_{last} + sum_j w_j y_j, then recurrence
@@ -109,6 +115,7 @@ SOp sop_inv(double a, double b, bool dag, int Ls, double mf) {
   o.c0 = c0;
   double rk = rho;
   for (int j = 0; j < Ls - 1; j++) { o.w[j] = -mf * rk * c0; rk *= rho; }
+  sop_round(o);
   return o;
 }
 SChain chain(SOp a = sop_none(), SOp b = sop_none()) {
@@ -241,7 +248,10 @@ void load_tune(mdwf_ctx* c) {
     TuneEntry e;
     char* end = nullptr;
     e.ns = (int)strtol(line.c_str() + n0 + 5, &end, 10);
-    if (end == line.c_str() + n0 + 5 || e.ns <= 0 || e.ns > 64) continue;  // corrupt entry: ignore
+    // corrupt entry: ignore (valid: 1..64 sites per CTA, optionally with the hop kernels'
+    // occupancy-bounded flag 1 << 16; a value no candidate list holds is ignored later too)
+    const int ns_only = e.ns & ~(1 << 16);
+    if (end == line.c_str() + n0 + 5 || e.ns <= 0 || ns_only <= 0 || ns_only > 64 || (e.ns >> 17) != 0) continue;
     e.ms = strtod(line.c_str() + m0 + 5, nullptr);
     c->tune[line.substr(q0 + 1, q1 - q0 - 1)] = e;
   }
@@ -314,6 +324,9 @@ int tuned_ns(mdwf_ctx* c, const std::string& key, const std::vector<int>& cands,
   *ns_out = best;
   return MDWF_SUCCESS;
 }
+
+// tuner value flag of the hop kernels: the occupancy-bounded build (sites per CTA in the low bits)
+constexpr int kOccBit = 1 << 16;
 
 std::vector<int> ns_candidates(int W, int maxthreads = MAXTHREADS) {
   std::vector<int> v;
@@ -406,24 +419,29 @@ int hop(mdwf_ctx* c, int prec, bool dag, const Field& in, const Field& out, int 
     for (int ns : ns_candidates(W)) {
       HopParams q = p;
       q.ns = ns;
-      if (hop_smem_bytes(prec, q, e.on) <= 200 * 1024) cands.push_back(ns);
+      if (hop_smem_bytes(prec, q, e.on) > 200 * 1024) continue;
+      cands.push_back(ns);
+      // fused 32-bit kernels also come in an occupancy-bounded build (tuner value | kOccBit)
+      if (e.on && prec != F64) cands.push_back(ns | kOccBit);
     }
   }
   if (cands.empty()) { g_last_error = "hop: shared memory"; return MDWF_ERR_ARG; }
-  const int dflt = std::min(ns_default(W), cands.back());
+  const int dflt = std::min(ns_default(W), cands.back() & ~kOccBit);
   const std::string key = key_of(c, dag ? "hopdag" : "hop", prec, in.nrhs,
                                  std::string(tc ? "tc" : "") + (e.on ? "epi" : "plain") + chain_sig(e.post) +
                                      chain_sig(e.fin) + (p.has_center ? "c" : "") + (p.axpy_r ? "a" : "") +
                                      (red.mode ? "r" : ""));
-  auto run = [&](int ns) -> int {
+  auto run = [&](int cfg) -> int {
     HopParams q = p;
+    const int ns = cfg & ~kOccBit;
     q.ns = ns;
     const long long blocks = (c->vh + ns - 1) / ns;
     if (q.red.mode != RED_NONE) {
       CKS(ensure_reduce(c, blocks, in.nrhs));
       q.red.partials = c->partials;
     }
-    cudaError_t err = tc ? launch_hop_tc(prec, dag, true, q, st) : launch_hop(prec, dag, r12, e.on, q, st);
+    cudaError_t err = tc ? launch_hop_tc(prec, dag, true, q, st)
+                         : launch_hop(prec, dag, r12, e.on, (cfg & kOccBit) != 0, q, st);
     c->launches++;
     c->bytes += half_bytes(in, prec) + gauge_bytes(c, prec) + (q.has_center ? half_bytes(e.center, prec) : 0.0) +
                 (q.axpy_r ? 2.0 * half_bytes(e.raxpy, prec) : half_bytes(out, prec));

@@ -8,7 +8,7 @@
 namespace mdwf {
 
 template <int P>
-cudaError_t launch_hop_prec(const HopParams& p, bool dag, bool r12, bool epi, int threads, size_t smem,
+cudaError_t launch_hop_prec(const HopParams& p, bool dag, bool r12, bool epi, bool occ, int threads, size_t smem,
                             cudaStream_t st);
 
 size_t hop_smem_bytes(int prec, const HopParams& p, bool epi) {
@@ -21,14 +21,14 @@ size_t hop_smem_bytes(int prec, const HopParams& p, bool epi) {
   return pre + epi_smem_bytes(csz, p.ns, p.in.nrhs, p.in.Ls, p.has_center, threads);
 }
 
-cudaError_t launch_hop(int prec, bool dag, bool r12, bool epi, const HopParams& p, cudaStream_t st) {
+cudaError_t launch_hop(int prec, bool dag, bool r12, bool epi, bool occ, const HopParams& p, cudaStream_t st) {
   const int threads = p.ns * p.in.nrhs * p.in.Ls;
   const size_t smem = hop_smem_bytes(prec, p, epi);
   switch (prec) {
-    case F64: return launch_hop_prec<F64>(p, dag, r12, epi, threads, smem, st);
-    case F32: return launch_hop_prec<F32>(p, dag, r12, epi, threads, smem, st);
-    case F16: return launch_hop_prec<F16>(p, dag, r12, epi, threads, smem, st);
-    case BF16: return launch_hop_prec<BF16>(p, dag, r12, epi, threads, smem, st);
+    case F64: return launch_hop_prec<F64>(p, dag, r12, epi, occ, threads, smem, st);
+    case F32: return launch_hop_prec<F32>(p, dag, r12, epi, occ, threads, smem, st);
+    case F16: return launch_hop_prec<F16>(p, dag, r12, epi, occ, threads, smem, st);
+    case BF16: return launch_hop_prec<BF16>(p, dag, r12, epi, occ, threads, smem, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -241,8 +241,11 @@ __device__ __forceinline__ typename PT<P>::C load_proj(const Field& f, unsigned 
 // Link staging stride in shared memory (compute-precision reals per link, 16-byte rows)
 template <typename C> __host__ __device__ constexpr int link_stride() { return sizeof(C) == 8 ? 18 : 20; }
 
-template <int P, bool DAG, bool R12, bool EPI>
-__global__ void __launch_bounds__(MAXTHREADS)
+// OCC: the occupancy-bounded build (at least 4 CTAs of MAXTHREADS per SM, i.e. at most 64
+// registers, a few spilled); the autotuner picks it or the unbounded one per kernel and
+// lattice (fused 32-bit kernels only)
+template <int P, bool DAG, bool R12, bool EPI, bool OCC>
+__global__ void __launch_bounds__(MAXTHREADS, OCC ? 4 : 0)
 hop_kernel(const __grid_constant__ HopParams p) {
   using C = typename PT<P>::C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -319,30 +322,38 @@ hop_kernel(const __grid_constant__ HopParams p) {
   }
 }
 
-template <int P, bool DAG, bool R12, bool EPI>
+template <int P, bool DAG, bool R12, bool EPI, bool OCC = false>
 static cudaError_t launch_one(const HopParams& p, int threads, size_t smem, cudaStream_t st) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(hop_kernel<P, DAG, R12, EPI>,
+    cudaError_t e = cudaFuncSetAttribute(hop_kernel<P, DAG, R12, EPI, OCC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   const long long blocks = (p.g.vh + p.ns - 1) / p.ns;
-  hop_kernel<P, DAG, R12, EPI><<<(unsigned)blocks, threads, smem, st>>>(p);
+  hop_kernel<P, DAG, R12, EPI, OCC><<<(unsigned)blocks, threads, smem, st>>>(p);
   return cudaGetLastError();
 }
 
-// all (dagger, 12-real links, epilogue) variants of one storage precision
+template <int P, bool DAG, bool R12>
+static cudaError_t launch_epi(const HopParams& p, bool occ, int threads, size_t smem, cudaStream_t st) {
+  if constexpr (P != F64) {
+    if (occ) return launch_one<P, DAG, R12, true, true>(p, threads, smem, st);
+  }
+  return launch_one<P, DAG, R12, true>(p, threads, smem, st);
+}
+
+// all (dagger, 12-real links, epilogue, occupancy-bounded) variants of one storage precision
 template <int P>
-cudaError_t launch_hop_prec(const HopParams& p, bool dag, bool r12, bool epi, int threads, size_t smem,
+cudaError_t launch_hop_prec(const HopParams& p, bool dag, bool r12, bool epi, bool occ, int threads, size_t smem,
                             cudaStream_t st) {
   if (dag) {
-    if (r12) return epi ? launch_one<P, true, true, true>(p, threads, smem, st) : launch_one<P, true, true, false>(p, threads, smem, st);
-    return epi ? launch_one<P, true, false, true>(p, threads, smem, st) : launch_one<P, true, false, false>(p, threads, smem, st);
+    if (r12) return epi ? launch_epi<P, true, true>(p, occ, threads, smem, st) : launch_one<P, true, true, false>(p, threads, smem, st);
+    return epi ? launch_epi<P, true, false>(p, occ, threads, smem, st) : launch_one<P, true, false, false>(p, threads, smem, st);
   }
-  if (r12) return epi ? launch_one<P, false, true, true>(p, threads, smem, st) : launch_one<P, false, true, false>(p, threads, smem, st);
-  return epi ? launch_one<P, false, false, true>(p, threads, smem, st) : launch_one<P, false, false, false>(p, threads, smem, st);
+  if (r12) return epi ? launch_epi<P, false, true>(p, occ, threads, smem, st) : launch_one<P, false, true, false>(p, threads, smem, st);
+  return epi ? launch_epi<P, false, false>(p, occ, threads, smem, st) : launch_one<P, false, false, false>(p, threads, smem, st);
 }
 
 }  // namespace mdwf

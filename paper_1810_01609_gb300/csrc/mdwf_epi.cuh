@@ -47,7 +47,7 @@ template <typename C>
 struct SNbr { int su, sl; C fu, fl; };
 template <typename C>
 __device__ __forceinline__ SNbr<C> s_nbr(const SOp& o, int s, int Ls, C mf) {
-  const C b = (C)o.b;
+  const C b = sop_b<C>(o);
   const int sp = s + 1 < Ls ? s + 1 : 0, sm = s > 0 ? s - 1 : Ls - 1;
   const C fp = s + 1 < Ls ? b : -b * mf, fm = s > 0 ? b : -b * mf;
   SNbr<C> n;
@@ -77,7 +77,7 @@ __device__ __forceinline__ void center_combine(const HopParams& p, long long x_c
   const C hc = (C)p.hc, cc = (C)p.cc;
   const SOp& o = p.cop.op[0];
   const bool bid = o.kind != SOP_NONE;
-  const C a = bid ? (C)o.a : (C)1;
+  const C a = bid ? sop_a<C>(o) : (C)1;
   SNbr<C> n = {s, s, (C)0, (C)0};
   if (bid) n = s_nbr<C>(o, s, Ls, (C)p.mf);
   const int cu = r * Ls + n.su, cl = r * Ls + n.sl;

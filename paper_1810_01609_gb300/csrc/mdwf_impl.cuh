@@ -193,7 +193,18 @@ struct SOp {
   double inv_a;  // 1/a
   double c0;     // 1 / (a (1 + mf rho^Ls)), rho = -b/a
   double w[MAXLS];  // w[k] = -mf rho^(k+1) c0, k = 0..Ls-2
+  // the same rounded to FP32 on the host: the 32-bit kernels read these, so that no
+  // double -> float conversion (an FP64-pipe instruction, scarce on GB300) runs per use
+  float fa, fb, finv_a, fc0;
+  float fw[MAXLS];
 };
+
+// coefficients in the compute type
+template <typename C> __device__ __forceinline__ C sop_a(const SOp& o) { if constexpr (sizeof(C) == 4) return o.fa; else return (C)o.a; }
+template <typename C> __device__ __forceinline__ C sop_b(const SOp& o) { if constexpr (sizeof(C) == 4) return o.fb; else return (C)o.b; }
+template <typename C> __device__ __forceinline__ C sop_inv_a(const SOp& o) { if constexpr (sizeof(C) == 4) return o.finv_a; else return (C)o.inv_a; }
+template <typename C> __device__ __forceinline__ C sop_c0(const SOp& o) { if constexpr (sizeof(C) == 4) return o.fc0; else return (C)o.c0; }
+template <typename C> __device__ __forceinline__ C sop_w(const SOp& o, int j) { if constexpr (sizeof(C) == 4) return o.fw[j]; else return (C)o.w[j]; }
 
 struct SChain {
   SOp op[2];
@@ -203,7 +214,7 @@ struct SChain {
 template <typename C>
 __device__ __forceinline__ void sop_apply(const SOp& o, bool up, C* y, int st, int Ls, C mf) {
   if (o.kind == SOP_BIDIAG) {
-    const C a = (C)o.a, b = (C)o.b;
+    const C a = sop_a<C>(o), b = sop_b<C>(o);
     if (up) {
       C y0 = y[0];
       for (int s = 0; s < Ls - 1; s++) y[s * st] = a * y[s * st] + b * y[(s + 1) * st];
@@ -216,18 +227,18 @@ __device__ __forceinline__ void sop_apply(const SOp& o, bool up, C* y, int st, i
   } else if (o.kind == SOP_INV) {
     // (a + b S)^-1 with S^Ls = -mf: the last (up) / first (down) entry from the closed
     // form sum, then a first-order recurrence back through the chain.
-    const C inv_a = (C)o.inv_a, b = (C)o.b;
+    const C inv_a = sop_inv_a<C>(o), b = sop_b<C>(o);
     if (up) {
-      C acc = (C)o.c0 * y[(Ls - 1) * st];
-      for (int j = 0; j < Ls - 1; j++) acc += (C)o.w[j] * y[j * st];
+      C acc = sop_c0<C>(o) * y[(Ls - 1) * st];
+      for (int j = 0; j < Ls - 1; j++) acc += sop_w<C>(o, j) * y[j * st];
       y[(Ls - 1) * st] = acc;
       for (int s = Ls - 2; s >= 0; s--) {
         acc = (y[s * st] - b * acc) * inv_a;
         y[s * st] = acc;
       }
     } else {
-      C acc = (C)o.c0 * y[0];
-      for (int j = 0; j < Ls - 1; j++) acc += (C)o.w[j] * y[(Ls - 1 - j) * st];
+      C acc = sop_c0<C>(o) * y[0];
+      for (int j = 0; j < Ls - 1; j++) acc += sop_w<C>(o, j) * y[(Ls - 1 - j) * st];
       y[0] = acc;
       for (int s = 1; s < Ls; s++) {
         acc = (y[s * st] - b * acc) * inv_a;
@@ -253,7 +264,7 @@ __device__ __forceinline__ void chain_apply(const SChain& ch, int comp, C* y, in
 template <typename C, int L>
 __device__ __forceinline__ void sop_col(const SOp& o, bool up, C (&y)[L], C mf) {
   if (o.kind == SOP_BIDIAG) {
-    const C a = (C)o.a, b = (C)o.b;
+    const C a = sop_a<C>(o), b = sop_b<C>(o);
     if (up) {
       const C y0 = y[0];
 #pragma unroll
@@ -266,18 +277,18 @@ __device__ __forceinline__ void sop_col(const SOp& o, bool up, C (&y)[L], C mf) 
       y[0] = a * y[0] - b * mf * yl;
     }
   } else if (o.kind == SOP_INV) {
-    const C inv_a = (C)o.inv_a, b = (C)o.b;
+    const C inv_a = sop_inv_a<C>(o), b = sop_b<C>(o);
     if (up) {
-      C acc = (C)o.c0 * y[L - 1];
+      C acc = sop_c0<C>(o) * y[L - 1];
 #pragma unroll
-      for (int j = 0; j < L - 1; j++) acc += (C)o.w[j] * y[j];
+      for (int j = 0; j < L - 1; j++) acc += sop_w<C>(o, j) * y[j];
       y[L - 1] = acc;
 #pragma unroll
       for (int s = L - 2; s >= 0; s--) { acc = (y[s] - b * acc) * inv_a; y[s] = acc; }
     } else {
-      C acc = (C)o.c0 * y[0];
+      C acc = sop_c0<C>(o) * y[0];
 #pragma unroll
-      for (int j = 0; j < L - 1; j++) acc += (C)o.w[j] * y[L - 1 - j];
+      for (int j = 0; j < L - 1; j++) acc += sop_w<C>(o, j) * y[L - 1 - j];
       y[0] = acc;
 #pragma unroll
       for (int s = 1; s < L; s++) { acc = (y[s] - b * acc) * inv_a; y[s] = acc; }

@@ -30,7 +30,8 @@ struct HopParams {
 };
 
 size_t hop_smem_bytes(int prec, const HopParams& p, bool epi);
-cudaError_t launch_hop(int prec, bool dag, bool r12, bool epi, const HopParams& p, cudaStream_t st);
+// occ: the occupancy-bounded build of a fused 32-bit kernel (ignored otherwise)
+cudaError_t launch_hop(int prec, bool dag, bool r12, bool epi, bool occ, const HopParams& p, cudaStream_t st);
 
 // tensor-core hop for F16/BF16 (returns cudaErrorNotSupported when the shape is not covered)
 bool hop_tc_supported(int prec, const HopParams& p, bool r12);
