@@ -332,7 +332,9 @@ static cudaError_t launch_one(const HopParams& p, int threads, size_t smem, cuda
     attr_set = true;
   }
   const long long blocks = (p.g.vh + p.ns - 1) / p.ns;
-  hop_kernel<P, DAG, R12, EPI, OCC><<<(unsigned)blocks, threads, smem, st>>>(p);
+  HopParams q = p;   // scalars rounded once for the 32-bit kernels
+  q.hcf = (float)p.hc; q.ccf = (float)p.cc; q.mff = (float)p.mf;
+  hop_kernel<P, DAG, R12, EPI, OCC><<<(unsigned)blocks, threads, smem, st>>>(q);
   return cudaGetLastError();
 }
 

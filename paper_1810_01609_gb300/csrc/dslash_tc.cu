@@ -302,7 +302,9 @@ static cudaError_t go_tc(const HopParams& p, cudaStream_t st) {
   const int threads = tc_threads(p);
   const size_t smem = hop_tc_smem_bytes(p);
   const long long blocks = (p.g.vh + p.ns - 1) / p.ns;
-  hop_mma_kernel<P, DAG><<<(unsigned)blocks, threads, smem, st>>>(p);
+  HopParams q = p;   // scalars rounded once for the 32-bit kernels
+  q.hcf = (float)p.hc; q.ccf = (float)p.cc; q.mff = (float)p.mf;
+  hop_mma_kernel<P, DAG><<<(unsigned)blocks, threads, smem, st>>>(q);
   return cudaGetLastError();
 }
 

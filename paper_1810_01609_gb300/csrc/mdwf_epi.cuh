@@ -74,12 +74,12 @@ __device__ __forceinline__ void center_combine(const HopParams& p, long long x_c
   const int Ls = f.Ls;
   const long long W = f.W();
   const int col = r * Ls + s;
-  const C hc = (C)p.hc, cc = (C)p.cc;
+  const C hc = pick<C>(p.hcf, p.hc), cc = pick<C>(p.ccf, p.cc);
   const SOp& o = p.cop.op[0];
   const bool bid = o.kind != SOP_NONE;
   const C a = bid ? sop_a<C>(o) : (C)1;
   SNbr<C> n = {s, s, (C)0, (C)0};
-  if (bid) n = s_nbr<C>(o, s, Ls, (C)p.mf);
+  if (bid) n = s_nbr<C>(o, s, Ls, pick<C>(p.mff, p.mf));
   const int cu = r * Ls + n.su, cl = r * Ls + n.sl;
   if constexpr (P == F64 || P == F32) {
     constexpr int NC = PT<P>::NC, CW = 24 / NC;
@@ -137,7 +137,7 @@ __device__ __forceinline__ double epi_output(const HopParams& p, long long x, in
   if (p.axpy_r) {
     C rv[24];
     load_site<P>(p.raxpy, x, col, rv);
-    const C a = (C)p.red.cg[r].alpha;
+    const C a = pick<C>(p.red.cg[r].alpha_f, p.red.cg[r].alpha);
     C n = 0;
 #pragma unroll
     for (int k = 0; k < 24; k++) { rv[k] -= a * v[k]; n += rv[k] * rv[k]; }
@@ -156,7 +156,7 @@ __device__ __forceinline__ void hop_epilogue(const HopParams& p, typename PT<P>:
   const int tid = threadIdx.x, nt = blockDim.x;
   const long long site0 = (long long)blockIdx.x * ns;
   const int nsites = ns * W;
-  const C mf = (C)p.mf, hc = (C)p.hc, cc = (C)p.cc;
+  const C mf = pick<C>(p.mff, p.mf), hc = pick<C>(p.hcf, p.hc), cc = pick<C>(p.ccf, p.cc);
   const bool has_post = p.post.op[0].kind != SOP_NONE;
   const bool has_fin = p.fin.op[0].kind != SOP_NONE;
   const int nitems = ns * nrhs * 24;

@@ -347,7 +347,15 @@ struct CGScalars {   // per right-hand side
   int hit;           // gamma <= stop2 seen
   int breakdown;
   int pad;
+  float alpha_f, beta_f;   // alpha, beta rounded once for the 32-bit kernels
+  int pad2[2];
 };
+
+// a scalar in the compute type: the FP32 copy for 32-bit kernels (no per-thread
+// double -> float conversion on the FP64 pipe), the double otherwise
+template <typename C> __device__ __forceinline__ C pick(float f, double d) {
+  if constexpr (sizeof(C) == 4) return f; else return (C)d;
+}
 
 struct Red {
   int mode;
@@ -413,6 +421,7 @@ __device__ inline void block_grid_reduce_sm(const Red& red, double* sm, int Ls, 
         } else {
           c.alpha = c.active ? c.gamma / tot : 0.0;
         }
+        c.alpha_f = (float)c.alpha;
       } else if (red.mode == RED_CG_BETA) {
         CGScalars& c = red.cg[r];
         if (c.active) {
@@ -423,6 +432,7 @@ __device__ inline void block_grid_reduce_sm(const Red& red, double* sm, int Ls, 
         } else {
           c.beta = 0.0;
         }
+        c.beta_f = (float)c.beta;
       }
     }
     __syncthreads();

@@ -26,6 +26,7 @@ struct HopParams {
   SChain fin;
   int axpy_r;         // r -= alpha[rhs] * out and reduce |r|^2 instead of storing out
   double mf;
+  float hcf, ccf, mff;   // hc, cc, mf rounded once for the 32-bit kernels
   Red red;
 };
 
@@ -47,6 +48,7 @@ struct SLParams {
   SChain chain;
   double ca, cb;        // scalars
   double mf;
+  float caf, cbf, mff;  // the same rounded once for the 32-bit kernels
   Red red;
 };
 

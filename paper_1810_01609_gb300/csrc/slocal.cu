@@ -31,18 +31,18 @@ __global__ void __launch_bounds__(MAXTHREADS) chain_kernel(const __grid_constant
   const int nitems = p.ns * nrhs * 24;
   for (int it = tid; it < nitems; it += blockDim.x) {
     if ((long long)blockIdx.x * p.ns + (it / 24) / nrhs >= p.vh) continue;
-    chain_apply_fast(p.chain, it % 24, tile + it * LsP, 1, Ls, (C)p.mf);
+    chain_apply_fast(p.chain, it % 24, tile + it * LsP, 1, Ls, pick<C>(p.mff, p.mf));
   }
   __syncthreads();
   if (active) {
     C v[24];
-    const C ca = (C)p.ca;
+    const C ca = pick<C>(p.caf, p.ca);
 #pragma unroll
     for (int k = 0; k < 24; k++) v[k] = ca * tile[(grp * 24 + k) * LsP + s];
     if (p.c.data) {
       C w[24];
       load_site<P>(p.c, x_cb, col, w);
-      const C cb = (C)p.cb;
+      const C cb = pick<C>(p.cbf, p.cb);
 #pragma unroll
       for (int k = 0; k < 24; k++) v[k] += cb * w[k];
     }
@@ -62,13 +62,13 @@ __global__ void __launch_bounds__(MAXTHREADS) axpby_kernel(const __grid_constant
   if (x_cb < p.vh) {
     C v[24];
     load_site<P>(p.b, x_cb, col, v);
-    const C ca = (C)p.ca;
+    const C ca = pick<C>(p.caf, p.ca);
 #pragma unroll
     for (int k = 0; k < 24; k++) v[k] *= ca;
     if (p.c.data) {
       C w[24];
       load_site<P>(p.c, x_cb, col, w);
-      const C cb = (C)p.cb;
+      const C cb = pick<C>(p.cbf, p.cb);
 #pragma unroll
       for (int k = 0; k < 24; k++) v[k] += cb * w[k];
     }
@@ -96,18 +96,19 @@ __global__ void __launch_bounds__(MAXTHREADS) cg_update_kernel(const __grid_cons
   const int r = col / Ls, s = col - r * Ls, grp = site_l * nrhs + r;
   C* tile = (C*)smem_raw;
   if (active) {
-    const double alpha = p.red.cg[r].alpha, beta = p.red.cg[r].beta;
+    const double alpha = p.red.cg[r].alpha;
     C pv[24], rv[24];
     load_site<P>(p.a, x_cb, col, pv);
-    if (alpha != 0.0) {
+    if (pick<CX>(p.red.cg[r].alpha_f, alpha) != (CX)0) {
       CX xv[24];
       load_site<PX>(p.x, x_cb, col, xv);
+      const CX ax = pick<CX>(p.red.cg[r].alpha_f, alpha);
 #pragma unroll
-      for (int k = 0; k < 24; k++) xv[k] += (CX)alpha * (CX)pv[k];
+      for (int k = 0; k < 24; k++) xv[k] += ax * (CX)pv[k];
       store_site<PX>(p.x, x_cb, col, xv);
     }
     load_site<P>(p.b, x_cb, col, rv);
-    const C bt = (C)beta;
+    const C bt = pick<C>(p.red.cg[r].beta_f, p.red.cg[r].beta);
 #pragma unroll
     for (int k = 0; k < 24; k++) { pv[k] = rv[k] + bt * pv[k]; tile[(grp * 24 + k) * LsP + s] = pv[k]; }
     store_site<P>(p.a, x_cb, col, pv);
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(MAXTHREADS) cg_update_kernel(const __grid_cons
   const int nitems = p.ns * nrhs * 24;
   for (int it = tid; it < nitems; it += blockDim.x) {
     if ((long long)blockIdx.x * p.ns + (it / 24) / nrhs >= p.vh) continue;
-    chain_apply_fast(p.chain, it % 24, tile + it * LsP, 1, Ls, (C)p.mf);
+    chain_apply_fast(p.chain, it % 24, tile + it * LsP, 1, Ls, pick<C>(p.mff, p.mf));
   }
   __syncthreads();
   if (active) {
@@ -202,7 +203,9 @@ static cudaError_t go(K kern, const SLParams& p, int W, size_t smem, cudaStream_
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  kern<<<(unsigned)blocks, p.ns * W, smem, st>>>(p);
+  SLParams q = p;   // scalars rounded once for the 32-bit kernels
+  q.caf = (float)p.ca; q.cbf = (float)p.cb; q.mff = (float)p.mf;
+  kern<<<(unsigned)blocks, p.ns * W, smem, st>>>(q);
   return cudaGetLastError();
 }
 
