@@ -328,10 +328,14 @@ int tuned_ns(mdwf_ctx* c, const std::string& key, const std::vector<int>& cands,
 // tuner value flag of the hop kernels: the occupancy-bounded build (sites per CTA in the low bits)
 constexpr int kOccBit = 1 << 16;
 
-std::vector<int> ns_candidates(int W, int maxthreads = MAXTHREADS) {
+// sites per CTA: powers of two, plus for the hop kernels (dense = true) every size up to
+// the thread limit (the wave count over 152 SMs matters as much as occupancy)
+std::vector<int> ns_candidates(int W, int maxthreads = MAXTHREADS, bool dense = false) {
   std::vector<int> v;
-  for (int ns = 1; ns <= 64; ns *= 2)
-    if (ns * W <= maxthreads) v.push_back(ns);
+  for (int ns = 1; ns <= 64; ns++) {
+    if (ns * W > maxthreads) break;
+    if (dense || (ns & (ns - 1)) == 0) v.push_back(ns);
+  }
   if (v.empty()) v.push_back(1);
   return v;
 }
@@ -416,7 +420,7 @@ int hop(mdwf_ctx* c, int prec, bool dag, const Field& in, const Field& out, int 
       if ((ns == 1 || ns * W <= 256) && hop_tc_smem_bytes(q) <= 200 * 1024) cands.push_back(ns);
     }
   } else {
-    for (int ns : ns_candidates(W)) {
+    for (int ns : ns_candidates(W, MAXTHREADS, true)) {
       HopParams q = p;
       q.ns = ns;
       if (hop_smem_bytes(prec, q, e.on) > 200 * 1024) continue;
