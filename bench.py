@@ -365,6 +365,11 @@ def mode_graphbatch(args):
         its.append(info.iterations)
     total = time.perf_counter() - t0
     lat64 = []
+    for k in ctxs:   # FP64 path warmed up per shape as well (its kernels tune on first use)
+        j = int(np.nonzero(draws == k)[0][0]) if np.any(draws == k) else None
+        if j is not None:
+            ctxs[k].solve(srcs[j], sloppy="f64", tol=1e-10, stream=stream)
+    torch.cuda.synchronize()
     for i in range(min(args.fp64_solves, 64)):
         t = time.perf_counter()
         ctxs[draws[i]].solve(srcs[i], sloppy="f64", tol=1e-10, stream=stream)
@@ -455,6 +460,9 @@ def main():
     for _ in range(args.warmup):
         step(b4, args.sloppy)
     barrier()
+    # where the timed region starts in a kernel launch list (the library's own launches;
+    # a profiler also counts the framework's few fills and copies)
+    print("library launches before the timed region: %d" % ctx.launch_count(), file=sys.stderr)
     sampler = ClockSampler(local)
     sampler.start()
     bytes0, launches0 = ctx.algorithmic_bytes(), ctx.launch_count()
@@ -473,10 +481,12 @@ def main():
     launches = ctx.launch_count() - launches0
     ms_step, value = replica_aggregate(ms / args.steps, step_bytes, dist, device="cuda")
 
-    # plain FP64 solve of the same source (same accuracy), once
+    # plain FP64 solve of the same source (same accuracy): one untimed solve (the FP64
+    # kernels tune on first use), then the timed one
     fp64 = None
     if not args.no_fp64:
         eta = ctx.make_source_4d(b4, nrhs=1, stream=stream)
+        ctx.solve(eta[0], sloppy="f64", tol=1e-10, stream=stream)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         x64, i64 = ctx.solve(eta[0], sloppy="f64", tol=1e-10, stream=stream)
