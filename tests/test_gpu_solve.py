@@ -125,3 +125,32 @@ def test_periodic_time_boundary():
     x, info = ctx.solve(b, tol=1e-10, sloppy="bf16")
     assert info.true_residual <= 1e-10
     assert rel(x, xo) <= 1e-8
+
+
+def test_incremental_residual_tracks_fp64():
+    """The reliable-update policy recomputes b~ - M x in FP64 only when the FP32 incremental
+    updates since the last recomputation could have drifted by 1 %: check, with the
+    MDWF_VERBOSE=2 trace (an FP64 recomputation beside every incremental update), that
+    they agree to 1 % on an 8^3 x 16 lattice with a light quark, F16 inner storage."""
+    import os
+    import re
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    prog = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "import inputs, torch, paper_1810_01609_gb300 as m\n"
+        "dims, Ls = (8, 8, 8, 16), 12\n"
+        "ctx = m.Context(dims, Ls, mf=0.01)\n"
+        "ctx.load_gauge(inputs.gauge_links(dims, 0.5, 7))\n"
+        "b = torch.from_numpy(inputs.gaussian_spinor5d(dims, Ls, 8)).cuda()\n"
+        "x, info = ctx.solve(b, sloppy='f16', tol=1e-10)\n"
+        "assert info.true_residual <= 1e-10, info.true_residual\n" % root)
+    env = dict(os.environ, MDWF_VERBOSE="2")
+    out = subprocess.run([sys.executable, "-c", prog], capture_output=True, text=True, env=env, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    pairs = [(float(a), float(b)) for a, b in
+             re.findall(r"incr residual ([0-9.e+-]+) \(fp64 ([0-9.e+-]+)\)", out.stderr)]
+    assert len(pairs) >= 2, out.stderr[-2000:]
+    for incr, fp64 in pairs:
+        assert abs(incr - fp64) <= 1e-2 * fp64, (incr, fp64)
