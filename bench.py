@@ -1,20 +1,22 @@
 """Benchmark of the MDWF propagator solve on GB300.
 
-Workload (default): 16^3 x 32 lattice, Ls = 12, Moebius b5 = 1.5, c5 = 0.5, M5 = 1.3,
-m_f = 0.02, synthetic links exp(i 0.4 H) reunitarised (Philox seed 2), one spin-colour
-point source at the origin.  One step = the point-source propagator column through the
-library's public calls: 4D source -> 5D source (Pauli-Villars injection), mixed-precision
-(F16 + norm storage, FP32 arithmetic, FP64 reliable updates) even-odd CG on the normal
-equations to a true FP64 relative residual of 1e-10, and the 4D projection.
+Workload (default, the precision configuration): 24^3 x 64 lattice, Ls = 10, Moebius
+b5 = 1.5, c5 = 0.5, M5 = 1.3, m_f = 0.01, synthetic links exp(i 0.5 H) reunitarised
+(Philox seed 3), one spin-colour point source at the origin.  One step = the point-source
+propagator column through the library's public calls: 4D source -> 5D source
+(Pauli-Villars injection), mixed-precision (F16 + norm storage, FP32 accumulation, FP64
+reliable updates) even-odd CG on the normal equations to a true FP64 relative residual of
+1e-10, and the 4D projection.
 
 Reported: value = algorithmic HBM GB/s of the whole step (bytes the library's kernels must
 move, counted by the library, divided by the step's device time), the mixed and the plain
 FP64 solve times to 1e-10 and their ratio, the roofline of the dominant kernel (the fused
-hop + M5^-1 kernel, timed alone with an L2 flush before every launch), end-to-end numbers
-through host buffers, SM clocks during the timed region and the FP64 CPU oracle timed on
-the host cores.
+hop + M5^-1 kernel, timed alone with an L2 flush before every launch), the same step end
+to end through the library's host-buffer path (MDWF_HOST pointers: the library copies
+in and out), SM clocks during the timed region, and the FP64 CPU oracle timed on the host
+cores (one core, and all cores on independent T-slabs of the lattice).
 
---impl reference runs the oracle (the FP64 numpy reference of the method) on the host
+--impl reference runs the oracle (the FP64 numpy reference of the method) on all host
 cores on a bounded sample of the same workload and prints the same JSON line.
 """
 import argparse
@@ -127,33 +129,98 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-_ORACLE_LINKS = {}
+def slab_dims(dims):
+    """A periodic T-slab of the lattice (the same X, Y, Z; T / 16, at least 2 and even)
+    whose oracle CG iteration costs about a sixteenth of the full one (the whole lattice when
+    T <= 8): the bounded sample
+    of the workload that the CPU baseline times (per-site arithmetic of the oracle does not
+    depend on the lattice extent)."""
+    X, Y, Z, T = dims
+    ts = T if T <= 8 else max(2, (T // 16) // 2 * 2)
+    return (X, Y, Z, ts)
 
 
-def cpu_oracle_sample(dims, Ls, mf, eps, seed, budget_s=20.0):
-    """Time CGNR iterations of the FP64 numpy oracle on the host cores (bounded sample)."""
+def oracle_slab_iterations(dims, Ls, mf, eps, seed, k, budget_s, max_iters=50):
+    """CGNR iterations (one M_pc and one M_pc^+ apply each) of the FP64 numpy oracle on
+    slab k of the workload (links and a Gaussian odd-site field drawn with seed*1000+k),
+    repeated until budget_s seconds have passed.  Returns (iterations, seconds); the link
+    and field generation is not timed."""
     import inputs
     from oracle import dirac
     from oracle.dirac import MobiusParams
-    key = (dims, eps, seed)
-    if key not in _ORACLE_LINKS:
-        _ORACLE_LINKS[key] = inputs.gauge_links(dims, eps, seed)
-    U = _ORACLE_LINKS[key]
+    sd = slab_dims(dims)
+    U = inputs.gauge_links(sd, eps, seed * 1000 + k)
     p = MobiusParams(Ls=Ls, mf=mf)
     Ub = dirac.boundary_links(U, -1.0)
-    par = dirac.parity_mask(dims)
-    x = dirac.on_parity(inputs.gaussian_spinor5d(dims, Ls, seed + 100), par, 1)
+    par = dirac.parity_mask(sd)
+    x = dirac.on_parity(inputs.gaussian_spinor5d(sd, Ls, seed * 1000 + k + 100), par, 1)
     t0 = time.perf_counter()
     its = 0
     while True:
-        q = dirac.mpc(Ub, x, p)                 # one CG iteration = M_pc and M_pc^+ applies
+        q = dirac.mpc(Ub, x, p)
         x = dirac.mpc_dag(Ub, q, p) * 1e-1
         its += 1
-        if time.perf_counter() - t0 >= budget_s or its >= 50:
+        if time.perf_counter() - t0 >= budget_s or its >= max_iters:
             break
-    dt = time.perf_counter() - t0
-    # the oracle's batched 3x3 / 4x4 numpy products run on one thread
-    return its, dt, 1
+    return its, time.perf_counter() - t0
+
+
+def _oracle_worker(a):
+    return oracle_slab_iterations(*a)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_oracle(dims, Ls, mf, eps, seed, budget_s, workers):
+    """Oracle throughput on the host cores, as GB/s of the GPU step's algorithmic bytes per
+    CG iteration: workers = 1 runs one slab in this process; workers > 1 runs one slab per
+    process in a spawn pool (independent slabs, together a CG iteration over the whole
+    lattice when workers = 16) and divides the bytes of all slabs by the slowest worker's
+    time.  Returns (GB/s, description, workers used)."""
+    sd = slab_dims(dims)
+    per_it = per_iteration_bytes(sd, Ls)
+    if workers <= 1:
+        its, dt = oracle_slab_iterations(dims, Ls, mf, eps, seed, 0, budget_s)
+        gbs = its * per_it / dt / 1e9
+        return gbs, "%d CGNR iteration(s) of the FP64 numpy oracle on one %s slab, Ls=%d, one process, %.1f s" % (
+            its, "x".join(map(str, sd)), Ls, dt), 1
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    # memory: about 12 slab-sized complex fields per worker
+    vol = sd[0] * sd[1] * sd[2] * sd[3] * Ls * 12 * 16
+    try:
+        mem = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+        workers = max(1, min(workers, int(mem * 0.5 // (12 * vol))))
+    except Exception:
+        pass
+    args = [(dims, Ls, mf, eps, seed, k, budget_s, 1) for k in range(workers)]
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_oracle_worker, args))
+    its = sum(r[0] for r in res)
+    dt = max(r[1] for r in res)
+    gbs = its * per_it / dt / 1e9
+    return gbs, ("%d CGNR iterations of the FP64 numpy oracle, one per process on %d independent %s slabs "
+                 "(Ls=%d) at once, %.1f s (slowest process)" % (its, workers, "x".join(map(str, sd)), Ls, dt)), workers
+
+
+def oracle_smallest_solve_s():
+    """Wall time of the oracle's full FP64 even-odd CG solve of the smallest configuration
+    (4^4, Ls 8, m_f 0.05, links eps 0.2 seed 1, point source) to 1e-10."""
+    import inputs
+    from oracle import dirac, solve
+    from oracle.dirac import MobiusParams
+    dims, Ls = (4, 4, 4, 4), 8
+    U = inputs.gauge_links(dims, 0.2, 1)
+    b = np.zeros((Ls,) + tuple(reversed(dims)) + (4, 3), dtype=np.complex128)
+    b[0, 0, 0, 0, 0, 0, 0] = 1.0
+    t0 = time.perf_counter()
+    _, its, _ = solve.solve_eo(dirac.boundary_links(U, -1.0), b, MobiusParams(Ls=Ls, mf=0.05), tol=1e-10)
+    return time.perf_counter() - t0, its
 
 
 def per_iteration_bytes(dims, Ls, nrhs=1):
@@ -189,23 +256,25 @@ def run_reference(args, wl):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    steps = []
-    cores = None
+    cores = min(16, host_cores())
+    vals, descs, ws = [], [], []
+    t_all = time.perf_counter()
     for i in range(args.warmup + args.steps):
-        its, dt, cores = cpu_oracle_sample(dims, Ls, mf, eps, seed, budget_s=args.ref_budget)
+        gbs, desc, w = cpu_oracle(dims, Ls, mf, eps, seed, args.ref_budget, cores)
         if i >= args.warmup:
-            steps.append((its, dt))
-    its = sum(s[0] for s in steps)
-    dt = sum(s[1] for s in steps)
-    gbs = its * per_iteration_bytes(dims, Ls) / dt / 1e9
-    sample = "%d CGNR iterations (M_pc + M_pc^+ applies) of the FP64 numpy oracle on %s, Ls=%d" % (
-        its, "x".join(map(str, dims)), Ls)
+            vals.append(gbs)
+            descs.append(desc)
+            ws.append(w)
+    gbs = float(np.mean(vals))
+    per_it = per_iteration_bytes(slab_dims(dims), Ls) * ws[-1]
     out = {"metric": METRIC, "value": gbs, "unit": "GB/s", "impl": "reference", "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / len(steps) * 1e3,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_it / (gbs * 1e9) * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": {"workload": wl, "lattice": list(dims), "Ls": Ls, "mf": mf},
-           "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
-           "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+           "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": ws[-1], "kind": "oracle",
+                            "sample": descs[-1] + "; per step"},
+           "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "wall_s": time.perf_counter() - t_all}
     print(json.dumps(out))
 
 
@@ -395,14 +464,14 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="16^3x32_Ls12", choices=sorted(WORKLOADS) + list(MODES))
+    ap.add_argument("--workload", default="24^3x64_Ls10", choices=sorted(WORKLOADS) + list(MODES))
     ap.add_argument("--group", type=int, default=3, help="batch32: right-hand sides per multi-RHS launch")
     ap.add_argument("--fp64-solves", type=int, default=16, help="graphbatch: solves repeated with plain FP64")
     ap.add_argument("--sloppy", default="f16", choices=["f16", "bf16", "f32"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--kernel-launches", type=int, default=20)
-    ap.add_argument("--ref-budget", type=float, default=12.0)
+    ap.add_argument("--ref-budget", type=float, default=8.0)
     ap.add_argument("--kernel-only", action="store_true",
                     help="only launch the fused hop + M5^-1 kernel a few times (for ncu captures)")
     ap.add_argument("--op", default="HOP_OE_M5INV")
@@ -486,13 +555,15 @@ def main():
     fp64 = None
     if not args.no_fp64:
         eta = ctx.make_source_4d(b4, nrhs=1, stream=stream)
-        ctx.solve(eta[0], sloppy="f64", tol=1e-10, stream=stream)
+        # a short FP64 solve first: the FP64 kernels tune on first use (untimed)
+        ctx.solve(eta[0], sloppy="f64", tol=1e-10, maxiter=30, check_interval=10, stream=stream)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        x64, i64 = ctx.solve(eta[0], sloppy="f64", tol=1e-10, stream=stream)
+        x64, i64 = ctx.solve(eta[0], sloppy="f64", tol=1e-10, full_residual=True, stream=stream)
         torch.cuda.synchronize()
         fp64 = {"ms": (time.perf_counter() - t0) * 1e3, "iterations": i64.iterations,
-                "true_residual": i64.true_residual}
+                "true_residual": i64.true_residual, "full_residual": i64.full_residual}
+        del x64
 
     # roofline leg: the fused hop + M5^-1 kernel (F16) timed alone, L2 flushed before each launch
     prec = m.PRECS[args.sloppy]
@@ -523,34 +594,47 @@ def main():
     achieved = kbytes / (kms * 1e-3) / 1e9
     del flush
 
-    # end to end through host buffers: pinned 4D source in, 4D propagator column out
+    # end to end through the library's host-buffer path: every call gets pinned HOST
+    # pointers and copies in and out itself (4D source in, 4D propagator column out)
+    sh5 = (1,) + ctx.shape5d()
     b4h = b4.cpu().pin_memory()
-    qh = torch.empty((1,) + ctx.shape4d(), dtype=torch.complex128).pin_memory()
+    eta_h = torch.empty(sh5, dtype=torch.complex128).pin_memory()
+    x_h = torch.empty(sh5, dtype=torch.complex128).pin_memory()
+    q_h = torch.empty((1,) + ctx.shape4d(), dtype=torch.complex128).pin_memory()
+    sp_host = ctx.solve_params(tol=1e-10, sloppy=args.sloppy, location=m.MDWF_HOST)
+
+    def step_host():
+        m.mdwf_make_source_4d(ctx.h, b4h, eta_h, 1, stream)
+        info = m.mdwf_solve(ctx.h, eta_h, x_h, sp_host, stream)
+        m.mdwf_project_4d(ctx.h, x_h, q_h, 1, stream)
+        return info
+
+    step_host()   # host-side staging buffers of the context are allocated here
     torch.cuda.synchronize()
     ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2e_bytes0 = ctx.algorithmic_bytes()
     ee0.record(stream)
     for _ in range(args.steps):
-        bd = b4h.to("cuda", non_blocking=True)
-        q, _ = step(bd, args.sloppy)
-        qh.copy_(q, non_blocking=True)
+        ih = step_host()
     ee1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = ee0.elapsed_time(ee1) / args.steps
     e2e_val = world * (ctx.algorithmic_bytes() - e2e_bytes0) / args.steps / (e2e_ms * 1e-3) / 1e9
+    b4b, b5b = b4h.numel() * 16, eta_h.numel() * 16
+    e2e_h2d = b4b + 2 * b5b      # source (make_source_4d), 5D source (solve), 5D solution (project_4d)
+    e2e_d2h = 2 * b5b + b4b      # 5D source, 5D solution, 4D propagator column
+    del eta_h, x_h
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        its, dt, cores = cpu_oracle_sample(dims, Ls, mf, eps, seed)
-        cgbs = its * per_iteration_bytes(dims, Ls) / dt / 1e9
-        try:
-            avail = len(os.sched_getaffinity(0))
-        except Exception:
-            avail = os.cpu_count()
-        cpu = {"value": cgbs, "unit": "GB/s", "cores": cores, "host_cores_available": avail, "kind": "oracle",
-               "sample": "%d CGNR iterations (M_pc + M_pc^+) of the FP64 numpy oracle on %s, Ls=%d, %.1f s; "
-                         "GB/s = the GPU step's algorithmic bytes per CG iteration x iterations / time"
-                         % (its, "x".join(map(str, dims)), Ls, dt)}
+        g1, d1, _ = cpu_oracle(dims, Ls, mf, eps, seed, args.ref_budget, 1)
+        cores = min(16, host_cores())
+        ga, da, wa = cpu_oracle(dims, Ls, mf, eps, seed, args.ref_budget, cores)
+        ts, tits = oracle_smallest_solve_s()
+        cpu = {"value": ga, "unit": "GB/s", "cores": wa, "host_cores_available": host_cores(), "kind": "oracle",
+               "sample": da + "; GB/s = the GPU step's algorithmic bytes per CG iteration x iterations / time",
+               "single_core": {"value": g1, "unit": "GB/s", "cores": 1, "sample": d1},
+               "oracle_solve_4^4_Ls8_s": ts, "oracle_solve_4^4_Ls8_iterations": tits}
 
     mixed_ms = float(np.mean([i.time_ms for i in infos]))
     out = {
@@ -566,9 +650,9 @@ def main():
         "solve": {"mixed_ms": mixed_ms, "iterations": infos[-1].iterations,
                   "reliable_updates": infos[-1].reliable_updates, "fp64_residuals": infos[-1].fp64_residuals,
                   "true_residual": infos[-1].true_residual,
-                  "full_residual": infos[-1].full_residual,
                   "fp64_ms": fp64["ms"] if fp64 else None, "fp64_iterations": fp64["iterations"] if fp64 else None,
                   "fp64_true_residual": fp64["true_residual"] if fp64 else None,
+                  "fp64_full_residual": fp64["full_residual"] if fp64 else None,
                   "speedup_vs_fp64": (fp64["ms"] / mixed_ms) if fp64 else None},
         "roofline": {"kernel": "fused hop + M5^-1 (HOP_OE_M5INV, %s)" % args.sloppy, "bound": "hbm",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
@@ -576,7 +660,9 @@ def main():
                      "bytes_per_launch": kbytes, "ms_per_launch": kms},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "GB/s", "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": int(b4h.numel() * 16), "d2h_bytes_per_step": int(qh.numel() * 16)},
+                "path": "mdwf_make_source_4d / mdwf_solve / mdwf_project_4d with pinned HOST pointers",
+                "true_residual": ih.true_residual,
+                "h2d_bytes_per_step": int(e2e_h2d), "d2h_bytes_per_step": int(e2e_d2h)},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }

@@ -119,7 +119,8 @@ typedef struct mdwf_solve_params {
   int check_interval;  /* iterations between host polls (and per captured CUDA graph) */
   int use_graph;       /* nonzero: replay the check_interval iterations as a CUDA graph */
   int location;        /* MDWF_HOST or MDWF_DEVICE for src / sol */
-  int full_residual;   /* nonzero: also compute |b - D x| / |b| (two extra FP64 hops) */
+  int full_residual;   /* nonzero: also compute |b - D x| / |b| (a diagnostic: two extra
+                          FP64 hops and a full-lattice FP64 pass) */
 } mdwf_solve_params;
 
 typedef struct mdwf_solve_info {
@@ -140,7 +141,7 @@ typedef struct mdwf_ctx mdwf_ctx;
  * recon 18, check_su3 1. */
 void mdwf_default_params(mdwf_params* p);
 /* Defaults: tol 1e-10, maxiter 100000, sloppy F16, delta 0.05, ru_interval 100,
- * check_interval 10, use_graph 1, location DEVICE, full_residual 1. */
+ * check_interval 10, use_graph 1, location DEVICE, full_residual 0. */
 void mdwf_default_solve_params(mdwf_solve_params* sp);
 
 /* Create a context on the current CUDA device.  Validates the parameters
@@ -218,11 +219,14 @@ int mdwf_contract_nucleon(mdwf_ctx* ctx, const double* u1, const double* d,
  * propagators; corr: T complex values), without any cudaMalloc or cudaFree: the per-site
  * scratch lives in a fixed 8 MiB array inside the library, which every GPU that loads the
  * library keeps until the process exits.  Lattices with more than 524288 4D sites are
- * rejected with MDWF_ERR_ARG (use mdwf_contract_nucleon).  The first call on each device
- * looks up the array's device address with that device current; make that first call
- * before any stream capture.  All calls share the array: calls whose kernels overlap on
- * the GPU (different streams, or the same call issued from several threads) race and
- * must be serialised by the caller.  Detail of a failure: mdwf_noalloc_last_error(). */
+ * rejected with MDWF_ERR_ARG (use mdwf_contract_nucleon), and so is a context created on
+ * another device than the current one.  Outside stream capture every call looks up the
+ * array's device address on the current device; a call made while `stream` is being
+ * captured reuses the address of this device's last uncaptured call, so make one call on
+ * each device before any capture (MDWF_ERR_STATE otherwise).  All calls share the array:
+ * calls whose kernels overlap on the GPU (different streams, or the same call issued from
+ * several threads) race and must be serialised by the caller.  Detail of a failure:
+ * mdwf_noalloc_last_error(). */
 int mdwf_contract_nucleon_noalloc(const mdwf_ctx* ctx, const double* u1, const double* d,
                                   const double* u2, double* corr, void* stream);
 const char* mdwf_noalloc_last_error(void);

@@ -45,7 +45,7 @@ class Context:
         return L.mdwf_field_bytes(self.h, L.PRECS.get(prec, prec), nrhs)
 
     def solve_params(self, tol=1e-10, sloppy="f16", maxiter=100000, delta=0.05, ru_interval=100, check_interval=10,
-                     use_graph=True, location=None, full_residual=True):
+                     use_graph=True, location=None, full_residual=False):
         sp = L.mdwf_default_solve_params()
         sp.tol, sp.maxiter, sp.sloppy_prec = tol, maxiter, L.PRECS.get(sloppy, sloppy)
         sp.delta, sp.ru_interval, sp.check_interval = delta, ru_interval, check_interval

@@ -59,6 +59,7 @@ struct DevBuf {
 
 struct mdwf_ctx {
   mdwf_params prm;
+  int device = -1;   // CUDA device current at mdwf_create: the context's buffers live there
   Geom g;
   int Ls;
   long long vh;
@@ -193,13 +194,23 @@ size_t field_bytes_of(const Field& f, int prec) {
   return (size_t)f.vh * prec_nc(prec) * f.nrhs * f.Ls * 16;
 }
 
+// Every instantiated CG graph holds the address of c->partials as a kernel parameter, so
+// the buffer is replaced only together with the graphs: a reallocation waits for the
+// device, frees the old buffer and destroys every graph (they are re-captured on their
+// next use, whose first block of iterations runs eagerly and sizes the buffer first).
 int ensure_reduce(mdwf_ctx* c, long long blocks, int nrhs) {
   const size_t need = (size_t)blocks * nrhs;
   if (need > c->partials_n) {
+    const size_t n = std::max(need, 2 * c->partials_n);
+    CK(cudaDeviceSynchronize());
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    c->graph_bytes.clear();
     if (c->partials) cudaFree(c->partials);
     c->partials = nullptr;
-    CK(cudaMalloc(&c->partials, need * sizeof(double)));
-    c->partials_n = need;
+    c->partials_n = 0;
+    CK(cudaMalloc(&c->partials, n * sizeof(double)));
+    c->partials_n = n;
   }
   return MDWF_SUCCESS;
 }
@@ -1027,7 +1038,7 @@ void mdwf_default_solve_params(mdwf_solve_params* sp) {
   if (!sp) return;
   sp->tol = 1e-10; sp->maxiter = 100000; sp->sloppy_prec = MDWF_PREC_F16; sp->delta = 0.05;
   sp->ru_interval = 100; sp->check_interval = 10; sp->use_graph = 1; sp->location = MDWF_DEVICE;
-  sp->full_residual = 1;
+  sp->full_residual = 0;
 }
 
 const char* mdwf_strerror(int s) {
@@ -1060,8 +1071,16 @@ int mdwf_create(const mdwf_params* p, mdwf_ctx** out) {
   }
   const double al = (4.0 - p->M5) * p->b5 + 1.0;
   if (al == 0.0) { g_last_error = "alpha = (4-M5) b5 + 1 must be nonzero"; return MDWF_ERR_ARG; }
+  // the device current now holds every buffer the context will allocate (no device at
+  // all is fine here: creation validates and allocates nothing)
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    dev = -1;
+    cudaGetLastError();
+  }
   mdwf_ctx* c = new mdwf_ctx();
   c->prm = *p;
+  c->device = dev;
   c->g.X = p->dims[0]; c->g.Y = p->dims[1]; c->g.Z = p->dims[2]; c->g.T = p->dims[3];
   c->g.Xh = p->dims[0] / 2;
   c->vh = (long long)p->dims[0] * p->dims[1] * p->dims[2] * p->dims[3] / 2;
@@ -1426,17 +1445,7 @@ int mdwf_contract_nucleon(mdwf_ctx* c, const double* u1, const double* d, const 
   void* site;
   CKS(ws_get(c, "nuc_site", (size_t)2 * c->vh * 16, &site));
   NucMats m;
-  const M4 g5 = mmul(mmul(gamma_mu(0), gamma_mu(1)), mmul(gamma_mu(2), gamma_mu(3)));
-  const M4 cg5 = mmul(mmul(gamma_mu(1), gamma_mu(3)), g5);
-  const M4 cg5b = mmul(mmul(gamma_mu(3), mdag(cg5)), gamma_mu(3));
-  const M4 g4 = gamma_mu(3);
-  for (int i = 0; i < 4; i++)
-    for (int j = 0; j < 4; j++) {
-      m.car[i * 4 + j] = cg5.m[i][j].real(); m.cai[i * 4 + j] = cg5.m[i][j].imag();
-      m.cbr[i * 4 + j] = cg5b.m[i][j].real(); m.cbi[i * 4 + j] = cg5b.m[i][j].imag();
-      const cd pv = 0.5 * ((i == j ? 1.0 : 0.0) + g4.m[i][j]);
-      m.pr[i * 4 + j] = pv.real(); m.pi[i * 4 + j] = pv.imag();
-    }
+  nucleon_mats(&m);
   CK(launch_nucleon(c->g, m, a, b, e, (double*)site, out, st));
   c->launches += 2;
   return finish_out(corr, out, (size_t)c->g.T * 16, where, st);
@@ -1482,6 +1491,8 @@ bool ctx_geom(const mdwf_ctx* c, Geom* g) {
   *g = c->g;
   return true;
 }
+
+int ctx_device(const mdwf_ctx* c) { return c ? c->device : -1; }
 
 // Spin matrices of the nucleon contraction in the library's chiral basis.
 void nucleon_mats(NucMats* m) {

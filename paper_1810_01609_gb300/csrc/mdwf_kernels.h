@@ -107,6 +107,9 @@ struct NucMats {          // row-major 4x4 complex spin matrices
   double cbr[16], cbi[16];  // gamma_4 (C gamma_5)^+ gamma_4
   double pr[16], pi[16];    // (1 + gamma_4)/2
 };
+// the spin matrices above in the library's chiral basis (host; one definition shared by
+// the regular and the allocation-free contraction)
+void nucleon_mats(NucMats* m);
 cudaError_t launch_nucleon(const Geom& g, const NucMats& m, const double* u1, const double* d,
                            const double* u2, double* site_tmp, double* corr, cudaStream_t st);
 

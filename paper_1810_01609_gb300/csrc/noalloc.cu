@@ -15,7 +15,7 @@
 
 namespace mdwf {
 bool ctx_geom(const mdwf_ctx* c, Geom* g);
-void nucleon_mats(NucMats* m);
+int ctx_device(const mdwf_ctx* c);
 }  // namespace mdwf
 
 using namespace mdwf;
@@ -61,12 +61,28 @@ int mdwf_contract_nucleon_noalloc(const mdwf_ctx* ctx, const double* u1, const d
     g_err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
     return MDWF_ERR_CUDA;
   }
+  // the propagators are device buffers of the context's device; the scratch array used
+  // is the current device's copy, so the two must be the same device
+  if (dev != ctx_device(ctx)) {
+    g_err = "the context was created on device " + std::to_string(ctx_device(ctx)) + " but device " +
+            std::to_string(dev) + " is current";
+    return MDWF_ERR_ARG;
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing((cudaStream_t)stream, &cap);
+  if (e != cudaSuccess) {
+    g_err = std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e);
+    return MDWF_ERR_CUDA;
+  }
   void* scratch = nullptr;
   {
-    // set-up once per device, with that device current: the host-side name of the array is
-    // not a device address, so the kernel gets the address the runtime reports for it
+    // The host-side name of the array is not a device address: the kernel gets the
+    // address the runtime reports for it, looked up with this device current.  Outside
+    // stream capture it is looked up on every call (cheap once the module is loaded, and
+    // correct again after a device reset reloads the module); during capture the address
+    // from this device's last uncaptured call is used.
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_nucleon_scratch);
       if (e != cudaSuccess || !p) {
@@ -74,6 +90,9 @@ int mdwf_contract_nucleon_noalloc(const mdwf_ctx* ctx, const double* u1, const d
         return MDWF_ERR_CUDA;
       }
       g_scratch_addr[dev] = p;
+    } else if (!g_scratch_addr[dev]) {
+      g_err = "the first call on a device must come before any stream capture";
+      return MDWF_ERR_STATE;
     }
     scratch = g_scratch_addr[dev];
   }

@@ -27,6 +27,30 @@ def rel(a, b):
     return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
 
 
+# Relative 2-norm tolerances of applies (whole output or sampled sites), and per-5D-site
+# bounds: max over sites of |got - ref|_site / rms_site(ref).  Rounding to 16 bits gives
+# a max-site / rms error ratio of 2.3 (F16 + norm) and 2.5 (BF16) times the relative
+# 2-norm error over 2M Gaussian sites, so the 16-bit site bounds are 2.5x the 2-norm
+# tolerance; FP64 / FP32 errors sit far below theirs.  A wrong tile, column or boundary
+# term gives O(1) at the sites it touches.
+TOL = {"f64": 1e-13, "f32": 1e-6, "f16": 2e-3, "bf16": 8e-3}
+SITE_TOL = {"f64": 1e-13, "f32": 1e-6, "f16": 5e-3, "bf16": 2e-2}
+
+
+def site_rel(got, ref, keep=None):
+    """max over 5D sites of |got - ref| / rms over sites of |ref|; a site is every index
+    but the trailing (spin, colour) axes.  keep: boolean mask broadcast against the site
+    axes (e.g. a [t, z, y, x] parity mask) selecting the sites compared."""
+    got = np.asarray(got)
+    ref = np.asarray(ref)
+    d = np.sqrt(np.sum(np.abs(got - ref) ** 2, axis=(-2, -1)))
+    r = np.sum(np.abs(ref) ** 2, axis=(-2, -1))
+    if keep is not None:
+        k = np.broadcast_to(keep, d.shape)
+        d, r = d[k], r[k]
+    return float(d.max() / np.sqrt(r.mean()))
+
+
 def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 

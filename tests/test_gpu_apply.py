@@ -1,18 +1,17 @@
 """GPU parity of the operator kernels (C ABI mdwf_apply / mdwf_pack / mdwf_unpack) against
 the FP64 oracle on the same seeded inputs.  Tolerances: relative 2-norm difference of the
 whole output, FP64 1e-13, FP32 1e-6, F16 (+norm) 2e-3, BF16 8e-3 (8 significant bits:
-unit roundoff 2^-9 on input and output)."""
+unit roundoff 2^-9 on input and output, plus the 16-bit projection and link rounding)."""
 import numpy as np
 import pytest
 
 import inputs
 from oracle import dirac, storage
 from oracle.dirac import MobiusParams
-from gpu_common import lib, rel, to_dev, to_host, parity_of, torch
+from gpu_common import lib, rel, site_rel, to_dev, to_host, parity_of, torch, TOL, SITE_TOL
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-13, "f32": 1e-6, "f16": 2e-3, "bf16": 8e-3}
 # (dims, Ls, nrhs): several tiles, ragged last tile for ns >= 16 (Vh = 72 = 8 * 9)
 CASES = [((4, 4, 4, 4), 8, 1), ((6, 2, 2, 6), 6, 1), ((4, 4, 4, 4), 5, 3)]
 
@@ -105,6 +104,8 @@ def test_apply_parity(case, prec, monkeypatch):
             assert not np.any(got[other]), op
         err = rel(got, ref)
         assert err <= TOL[prec], (op, prec, err)
+        serr = site_rel(got, ref, keep)
+        assert serr <= SITE_TOL[prec], (op, prec, "per site", serr)
 
 
 @pytest.mark.parametrize("prec", ["f16", "bf16"])

@@ -95,3 +95,23 @@ def test_graph_and_eager_iterations_agree():
     assert ig.iterations == ie.iterations
     assert torch.equal(xg, xe)
     assert ctx.launch_count() > 0 and ctx.algorithmic_bytes() > 0
+
+
+def test_graph_survives_reduction_buffer_growth():
+    """A captured CG graph holds the reduction-partials buffer's address.  A 12-RHS solve
+    in between needs a larger buffer; the graph replayed afterwards must not write into the
+    freed one: the third solve (graph) equals an eager solve bit for bit."""
+    m = lib()
+    ctx = _ctx(m, dims=(4, 4, 4, 8), Ls=4)
+    b1 = to_dev(inputs.gaussian_spinor5d(ctx.dims, ctx.Ls, 11))
+    b12 = to_dev(inputs.gaussian_spinor5d(ctx.dims, ctx.Ls, 12, nrhs=12))
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        x0, i0 = ctx.solve(b1, sloppy="f16", tol=1e-10, use_graph=True, stream=s)
+        xm, im = ctx.solve_multi(b12, sloppy="f16", tol=1e-10, use_graph=True, stream=s)
+        xg, ig = ctx.solve(b1, sloppy="f16", tol=1e-10, use_graph=True, stream=s)
+        xe, ie = ctx.solve(b1, sloppy="f16", tol=1e-10, use_graph=False, stream=s)
+    torch.cuda.synchronize()
+    assert all(i.true_residual <= 1e-10 for i in im)
+    assert ig.true_residual <= 1e-10 and ig.iterations == ie.iterations
+    assert torch.equal(xg, xe) and torch.equal(x0, xe)

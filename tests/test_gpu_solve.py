@@ -29,7 +29,7 @@ def test_solve_matches_oracle(sloppy, use_graph):
     U, Ub, p, b, xo = _problem(dims, Ls, mf)
     ctx = m.Context(dims, Ls, mf=mf)
     ctx.load_gauge(U)
-    x, info = ctx.solve(to_dev(b), tol=1e-10, sloppy=sloppy, use_graph=use_graph)
+    x, info = ctx.solve(to_dev(b), tol=1e-10, sloppy=sloppy, use_graph=use_graph, full_residual=True)
     x = to_host(x)
     assert info.status == 0
     assert info.true_residual <= 1e-10

@@ -40,3 +40,36 @@ def test_noalloc_rejects_oversized_lattice():
         m.mdwf_contract_nucleon_noalloc(ctx.h, small, small, small, small)
     assert e.value.code == m.MDWF_ERR_ARG
     assert "at most 524288" in str(e.value)
+
+
+def test_noalloc_captured_in_graph_and_allocates_nothing():
+    """The use it exists for: after one warm call, the call is captured in a CUDA graph
+    on a side stream and replayed with new propagator contents; and a warm call leaves the
+    device's free memory unchanged."""
+    m = lib()
+    ctx = m.Context((4, 4, 2, 8), 4)
+    T = ctx.dims[3]
+    props = [to_dev(p) for p in _props(ctx, 31)]
+    got = torch.zeros(T, dtype=torch.complex128, device="cuda")
+    ref = torch.empty(T, dtype=torch.complex128, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        m.mdwf_contract_nucleon_noalloc(ctx.h, *props, got, stream=s)   # warm call (set-up)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    with torch.cuda.stream(s):
+        m.mdwf_contract_nucleon_noalloc(ctx.h, *props, got, stream=s)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        m.mdwf_contract_nucleon_noalloc(ctx.h, *props, got, stream=s)
+    for seed in (32, 33):
+        for dst, src in zip(props, _props(ctx, seed)):
+            dst.copy_(to_dev(src))
+        got.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        m.mdwf_contract_nucleon(ctx.h, *props, ref)
+        torch.cuda.synchronize()
+        assert rel(to_host(got), to_host(ref)) <= 1e-13, seed
