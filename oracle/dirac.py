@@ -113,8 +113,8 @@ def s_apply(Mm, Mp, psi):
 
 
 def s_matrices(p, which, dagger=False, mf=None):
-    """(Mm, Mp) of one s-operator: 'B', 'D5', 'A5', 'A5inv'.  The inverse is a plain
-    dense inverse of the matrix built from the definition."""
+    """(Mm, Mp) of one s-operator: 'B', 'D5', 'A5', 'A5inv', 'D5inv'.  The inverses are
+    plain dense inverses of the matrices built from the definition."""
     mf = p.mf if mf is None else mf
     Bm, Bp = b_matrices(p.Ls, mf)
     I = np.eye(p.Ls)
@@ -127,6 +127,9 @@ def s_matrices(p, which, dagger=False, mf=None):
     elif which == "A5inv":
         mats = (np.linalg.inv(p.alpha * I + p.beta * Bm),
                 np.linalg.inv(p.alpha * I + p.beta * Bp))
+    elif which == "D5inv":
+        mats = (np.linalg.inv(p.b5 * I + p.c5 * Bm),
+                np.linalg.inv(p.b5 * I + p.c5 * Bp))
     else:
         raise ValueError(which)
     if dagger:  # real matrices: adjoint = transpose
@@ -177,6 +180,25 @@ def mpc_dag(Ub, psi_o, p):
     """M_pc^dagger = 1 - (1/4) D5^+ H_eo^+ A5^-+ D5^+ H_oe^+ A5^-+ (H^+ = gamma5 H gamma5)."""
     t = s_op(p, "D5", hop(Ub, s_op(p, "A5inv", psi_o, dagger=True), dagger=True), dagger=True)
     u = s_op(p, "D5", hop(Ub, s_op(p, "A5inv", t, dagger=True), dagger=True), dagger=True)
+    return psi_o - 0.25 * u
+
+
+def mpc_sym(Ub, psi_o, p):
+    """Symmetric even-odd form.  D D5^-1 = [[A~, -H_eo/2], [-H_oe/2, A~]] with the
+    s-local diagonal block A~ = A5 D5^-1; its odd-site Schur complement with both
+    diagonal inverses on the left of their hops is
+        M_sym = 1 - (1/4) A~^-1 H_oe A~^-1 H_eo,   A~^-1 = D5 A5^-1
+    (= D5 M_pc D5^-1).  The odd system M_sym y = D5 b~_o gives x_o = D5^-1 y."""
+    t = s_op(p, "D5", s_op(p, "A5inv", hop(Ub, psi_o)))
+    u = s_op(p, "D5", s_op(p, "A5inv", hop(Ub, t)))
+    return psi_o - 0.25 * u
+
+
+def mpc_sym_dag(Ub, psi_o, p):
+    """M_sym^dagger = 1 - (1/4) (H^+)_oe A~^-+ (H^+)_eo A~^-+,  A~^-+ = A5^-+ D5^+."""
+    xd = lambda f: s_op(p, "A5inv", s_op(p, "D5", f, dagger=True), dagger=True)
+    t = hop(Ub, xd(psi_o), dagger=True)
+    u = hop(Ub, xd(t), dagger=True)
     return psi_o - 0.25 * u
 
 

@@ -63,6 +63,18 @@ def solve_eo(Ub, b, p, tol=1e-10, maxiter=100000):
     return dirac.reconstruct(Ub, b, xo, p, par), it, res
 
 
+def solve_eo_sym(Ub, b, p, tol=1e-10, maxiter=100000):
+    """The same solution through the symmetric form: CGNR on M_sym y = D5 b~_o, then
+    x_o = D5^-1 y.  Returns (x, iterations, true relative residual of that system)."""
+    dims = (b.shape[-3], b.shape[-4], b.shape[-5], b.shape[-6])
+    par = dirac.parity_mask(dims)
+    rhs = dirac.s_op(p, "D5", dirac.prepare_source(Ub, b, p, par))
+    A = lambda v: dirac.mpc_sym(Ub, v, p)
+    Ad = lambda v: dirac.mpc_sym_dag(Ub, v, p)
+    y, it, res = cgnr(A, Ad, rhs, tol, maxiter)
+    return dirac.reconstruct(Ub, b, dirac.s_op(p, "D5inv", y), p, par), it, res
+
+
 def solve_full(Ub, b, p, tol=1e-10, maxiter=100000, mf=None):
     """Unpreconditioned route: CGNR on the full 5D operator D (independent check of the
     even-odd machinery)."""

@@ -77,6 +77,8 @@ struct mdwf_ctx {
   double* red_host = nullptr;  // pinned [256]
   CGScalars* cg = nullptr;     // device [64]
   CGScalars* cg_host = nullptr;
+  int* dev_status = nullptr;   // device flag set by a kernel whose bounded wait gave up
+  int* status_host = nullptr;  // pinned copy
   // tuning
   bool tuning = true;
   std::map<std::string, TuneEntry> tune;
@@ -259,10 +261,12 @@ void load_tune(mdwf_ctx* c) {
     TuneEntry e;
     char* end = nullptr;
     e.ns = (int)strtol(line.c_str() + n0 + 5, &end, 10);
-    // corrupt entry: ignore (valid: 1..64 sites per CTA, optionally with the hop kernels'
-    // occupancy-bounded flag 1 << 16; a value no candidate list holds is ignored later too)
-    const int ns_only = e.ns & ~(1 << 16);
-    if (end == line.c_str() + n0 + 5 || e.ns <= 0 || ns_only <= 0 || ns_only > 64 || (e.ns >> 17) != 0) continue;
+    // corrupt entry: ignore (valid: 1..64 sites per CTA, optionally with one of the hop
+    // kernels' flags 1 << 16 (occupancy-bounded build) or 1 << 17 (tensor-core kernel); a
+    // value no candidate list holds is ignored later too)
+    const int ns_only = e.ns & 0xFFFF;
+    const int flags = e.ns >> 16;
+    if (end == line.c_str() + n0 + 5 || e.ns <= 0 || ns_only <= 0 || ns_only > 64 || flags > 2) continue;
     e.ms = strtod(line.c_str() + m0 + 5, nullptr);
     c->tune[line.substr(q0 + 1, q1 - q0 - 1)] = e;
   }
@@ -274,6 +278,11 @@ bool capturing(cudaStream_t st) {
   return s != cudaStreamCaptureStatusNone;
 }
 
+// tuner value flags of the hop kernels (sites per CTA in the low 16 bits): the
+// occupancy-bounded build of the CUDA-core kernel, and the tcgen05 tensor-core kernel
+constexpr int kOccBit = 1 << 16;
+constexpr int kTcBit = 1 << 17;
+
 // Pick sites-per-CTA for `key` by brute force over `cands`, timing each with events.
 // In-place outputs listed in `snaps` are saved before and restored after every trial run,
 // so tuning does not change the result of the call.
@@ -283,7 +292,8 @@ int tuned_ns(mdwf_ctx* c, const std::string& key, const std::vector<int>& cands,
   // MDWF_FORCE_NS pins sites-per-CTA (tests use it to exercise ragged last tiles)
   if (const char* fns = getenv("MDWF_FORCE_NS")) {
     const int f = atoi(fns);
-    if (std::find(cands.begin(), cands.end(), f) != cands.end()) { *ns_out = f; return MDWF_SUCCESS; }
+    for (int v : {f, f | kTcBit})
+      if (std::find(cands.begin(), cands.end(), v) != cands.end()) { *ns_out = v; return MDWF_SUCCESS; }
   }
   auto it = c->tune.find(key);
   if (it != c->tune.end()) {
@@ -336,8 +346,6 @@ int tuned_ns(mdwf_ctx* c, const std::string& key, const std::vector<int>& cands,
   return MDWF_SUCCESS;
 }
 
-// tuner value flag of the hop kernels: the occupancy-bounded build (sites per CTA in the low bits)
-constexpr int kOccBit = 1 << 16;
 
 // sites per CTA: powers of two, plus for the hop kernels (dense = true) every size up to
 // the thread limit (the wave count over 152 SMs matters as much as occupancy)
@@ -420,17 +428,14 @@ int hop(mdwf_ctx* c, int prec, bool dag, const Field& in, const Field& out, int 
   p.red = red;
   const bool r12 = c->prm.gauge_recon == 12;
   const int W = in.nrhs * in.Ls;
-  // MDWF_TC=1 selects the tensor-core kernel (one warp per 4D site) for F16 / BF16 storage
+  // F16 / BF16: the tcgen05 tensor-core kernel (tuner value | kTcBit, sites per CTA in the
+  // low bits) competes with the CUDA-core kernel; MDWF_TC=0 leaves it out, MDWF_TC=1 uses
+  // it alone
   const char* use_tc = getenv("MDWF_TC");
-  const bool tc = (use_tc && use_tc[0] == '1') && hop_tc_supported(prec, p, r12);
+  const bool tc_ok = hop_tc_supported(prec, p, r12) && !(use_tc && use_tc[0] == '0');
+  const bool tc_only = tc_ok && use_tc && use_tc[0] == '1';
   std::vector<int> cands;
-  if (tc) {
-    for (int ns = 1; ns <= 32; ns *= 2) {
-      HopParams q = p;
-      q.ns = ns;
-      if ((ns == 1 || ns * W <= 256) && hop_tc_smem_bytes(q) <= 200 * 1024) cands.push_back(ns);
-    }
-  } else {
+  if (!tc_only) {
     for (int ns : ns_candidates(W, MAXTHREADS, true)) {
       HopParams q = p;
       q.ns = ns;
@@ -440,22 +445,39 @@ int hop(mdwf_ctx* c, int prec, bool dag, const Field& in, const Field& out, int 
       if (e.on && prec != F64) cands.push_back(ns | kOccBit);
     }
   }
+  if (tc_ok) {
+    for (int ns = 1; ns <= 16; ns *= 2) {
+      HopParams q = p;
+      q.ns = ns;
+      if (hop_tc_smem_bytes(q) > 200 * 1024 || hop_tc_tmem_cols(q) > 256) break;
+      cands.push_back(ns | kTcBit);
+    }
+  }
   if (cands.empty()) { g_last_error = "hop: shared memory"; return MDWF_ERR_ARG; }
-  const int dflt = std::min(ns_default(W), cands.back() & ~kOccBit);
+  int dflt = cands.front();
+  if (tc_only) {
+    dflt = cands.back();
+    for (int v : cands) if ((v & 0xFFFF) == 4) dflt = v;
+  } else {
+    const int want = std::min(ns_default(W), cands.back() & 0xFFFF);
+    for (int v : cands) if (v == want) dflt = v;
+  }
   const std::string key = key_of(c, dag ? "hopdag" : "hop", prec, in.nrhs,
-                                 std::string(tc ? "tc" : "") + (e.on ? "epi" : "plain") + chain_sig(e.post) +
+                                 std::string(tc_only ? "tc" : "") + (e.on ? "epi" : "plain") + chain_sig(e.post) +
                                      chain_sig(e.fin) + (p.has_center ? "c" : "") + (p.axpy_r ? "a" : "") +
                                      (red.mode ? "r" : ""));
   auto run = [&](int cfg) -> int {
     HopParams q = p;
-    const int ns = cfg & ~kOccBit;
+    const int ns = cfg & 0xFFFF;
+    const bool tc = (cfg & kTcBit) != 0;
     q.ns = ns;
+    q.status = c->dev_status;
     const long long blocks = (c->vh + ns - 1) / ns;
     if (q.red.mode != RED_NONE) {
       CKS(ensure_reduce(c, blocks, in.nrhs));
       q.red.partials = c->partials;
     }
-    cudaError_t err = tc ? launch_hop_tc(prec, dag, true, q, st)
+    cudaError_t err = tc ? launch_hop_tc(prec, dag, r12, e.on, q, st)
                          : launch_hop(prec, dag, r12, e.on, (cfg & kOccBit) != 0, q, st);
     c->launches++;
     c->bytes += half_bytes(in, prec) + gauge_bytes(c, prec) + (q.has_center ? half_bytes(e.center, prec) : 0.0) +
@@ -704,10 +726,21 @@ int cg_iteration(mdwf_ctx* c, const CGSet& v, cudaStream_t st) {
   return run(ns);
 }
 
+// the device status flag (a kernel whose bounded wait gave up) -> MDWF_ERR_TIMEOUT
+int check_status(mdwf_ctx* c, cudaStream_t st) {
+  CK(cudaMemcpyAsync(c->status_host, c->dev_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (*c->status_host) {
+    CK(cudaMemsetAsync(c->dev_status, 0, sizeof(int), st));
+    g_last_error = "a tensor-core hop kernel gave up waiting for its matrix products";
+    return MDWF_ERR_TIMEOUT;
+  }
+  return MDWF_SUCCESS;
+}
+
 int pull_scalars(mdwf_ctx* c, int nrhs, cudaStream_t st) {
   CK(cudaMemcpyAsync(c->cg_host, c->cg, nrhs * sizeof(CGScalars), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  return MDWF_SUCCESS;
+  return check_status(c, st);
 }
 int push_scalars(mdwf_ctx* c, int nrhs, cudaStream_t st) {
   CK(cudaMemcpyAsync(c->cg, c->cg_host, nrhs * sizeof(CGScalars), cudaMemcpyHostToDevice, st));
@@ -1106,8 +1139,10 @@ void mdwf_destroy(mdwf_ctx* c) {
   if (c->counter) cudaFree(c->counter);
   if (c->red_out) cudaFree(c->red_out);
   if (c->cg) cudaFree(c->cg);
+  if (c->dev_status) cudaFree(c->dev_status);
   if (c->red_host) cudaFreeHost(c->red_host);
   if (c->cg_host) cudaFreeHost(c->cg_host);
+  if (c->status_host) cudaFreeHost(c->status_host);
   delete c;
 }
 
@@ -1118,6 +1153,9 @@ static int ensure_small(mdwf_ctx* c) {
   CK(cudaMalloc(&c->red_out, 256 * sizeof(double)));
   CK(cudaMalloc(&c->cg, 64 * sizeof(CGScalars)));
   CK(cudaMemset(c->cg, 0, 64 * sizeof(CGScalars)));
+  CK(cudaMalloc(&c->dev_status, sizeof(int)));
+  CK(cudaMemset(c->dev_status, 0, sizeof(int)));
+  CK(cudaMallocHost(&c->status_host, sizeof(int)));
   CK(cudaMallocHost(&c->red_host, 256 * sizeof(double)));
   CK(cudaMallocHost(&c->cg_host, 64 * sizeof(CGScalars)));
   return MDWF_SUCCESS;

@@ -28,16 +28,18 @@ struct HopParams {
   double mf;
   float hcf, ccf, mff;   // hc, cc, mf rounded once for the 32-bit kernels
   Red red;
+  int* status;        // device flag: nonzero once a bounded device-side wait gave up
 };
 
 size_t hop_smem_bytes(int prec, const HopParams& p, bool epi);
 // occ: the occupancy-bounded build of a fused 32-bit kernel (ignored otherwise)
 cudaError_t launch_hop(int prec, bool dag, bool r12, bool epi, bool occ, const HopParams& p, cudaStream_t st);
 
-// tensor-core hop for F16/BF16 (returns cudaErrorNotSupported when the shape is not covered)
+// tcgen05 tensor-core hop for F16 / BF16 storage (dslash_umma.cu); p.ns = 4D sites per CTA
 bool hop_tc_supported(int prec, const HopParams& p, bool r12);
-size_t hop_tc_smem_bytes(const HopParams& p);   // p.ns = warps (4D sites) per CTA
-cudaError_t launch_hop_tc(int prec, bool dag, bool epi, const HopParams& p, cudaStream_t st);
+size_t hop_tc_smem_bytes(const HopParams& p);
+int hop_tc_tmem_cols(const HopParams& p);        // tensor-memory columns one CTA allocates
+cudaError_t launch_hop_tc(int prec, bool dag, bool r12, bool epi, const HopParams& p, cudaStream_t st);
 
 // ---------------------------------------------------------------- s-local kernels (slocal.cu)
 struct SLParams {

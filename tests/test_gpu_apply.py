@@ -108,18 +108,45 @@ def test_apply_parity(case, prec, monkeypatch):
         assert serr <= SITE_TOL[prec], (op, prec, "per site", serr)
 
 
+TC_CASES = CASES + [((4, 4, 4, 8), 12, 12), ((4, 2, 2, 4), 10, 2)]
+
+
 @pytest.mark.parametrize("prec", ["f16", "bf16"])
-def test_tensor_core_hop_matches_oracle(prec, monkeypatch):
-    """The mma.sync hop kernel (MDWF_TC=1) on every hop-based op, several tiles + ragged."""
+@pytest.mark.parametrize("force_ns", [None, "1", "16"])
+def test_tensor_core_hop_matches_oracle(prec, force_ns, monkeypatch):
+    """The tcgen05 hop kernel (MDWF_TC=1) on every hop-based op: several tiles, a ragged
+    last tile (16 sites per CTA on a 72-site half lattice), Ls 5..12, up to 12 RHS
+    (144 accumulator columns per site, several 16-column TMEM loads)."""
     monkeypatch.setenv("MDWF_TC", "1")
-    for case in CASES:
+    if force_ns:
+        monkeypatch.setenv("MDWF_FORCE_NS", force_ns)
+    for case in TC_CASES:
         dims, Ls, nrhs = case
+        if force_ns == "16" and nrhs * Ls > 16:
+            continue          # 16 sites of more than 16 columns exceed the tensor-memory budget
         m, ctx, U, Ub, psi, p = _setup(dims, Ls, nrhs)
         par = parity_of(dims)
-        for op in ["HOP_EO", "HOP_OE_DAG", "HOP_OE_M5INV", "MPC", "MPC_DAG", "FULL_D"]:
+        for op in ["HOP_EO", "HOP_OE_DAG", "HOP_OE_M5INV", "MPC", "MPC_DAG", "MDAGM", "FULL_D", "FULL_D_DAG"]:
             got = _gpu_apply(m, ctx, op, prec, psi, nrhs)
             ref = np.stack([_oracle(op, Ub, psi[r], p, par) for r in range(nrhs)])
+            keep = _mask(op, par, ref.shape)
             assert rel(got, ref) <= TOL[prec], (op, prec, case)
+            assert site_rel(got, ref, keep) <= SITE_TOL[prec], (op, prec, case, "per site")
+
+
+@pytest.mark.parametrize("prec", ["f16", "bf16"])
+def test_tensor_core_hop_recon12(prec, monkeypatch):
+    """12-real links (third row rebuilt in the tensor-core kernel's link-matrix build,
+    with the time-boundary sign) against the 18-real result."""
+    monkeypatch.setenv("MDWF_TC", "1")
+    dims, Ls = (4, 4, 4, 4), 6
+    outs = []
+    for recon in (18, 12):
+        m, ctx, U, Ub, psi, p = _setup(dims, Ls, 1, recon=recon)
+        outs.append(_gpu_apply(m, ctx, "MPC", prec, psi, 1))
+    par = parity_of(dims)
+    ref = _oracle("MPC", Ub, psi[0], p, par)
+    assert rel(outs[1][0], ref) <= TOL[prec] and rel(outs[0][0], ref) <= TOL[prec]
 
 
 def test_recon12_matches_recon18():

@@ -68,7 +68,7 @@ def _tuned_tiles(ctx, tag="hop"):
     return sorted(out) or [1]
 
 
-def _sites(dims, parity, tiles, seed, n_random=1000, n_tiles=500):
+def _sites(dims, parity, tiles, seed, n_random=2000, n_tiles=500):
     """>= 2000 sites of one parity (None: both): random ones, the first and last site of
     n_tiles random tiles of every tile size, the whole last tile, lattice corners."""
     X, Y, Z, T = dims

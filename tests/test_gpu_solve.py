@@ -23,7 +23,13 @@ def _problem(dims=(4, 4, 4, 4), Ls=8, mf=0.05, eps=0.2, seed=1):
 
 @pytest.mark.parametrize("sloppy", ["f64", "f32", "f16", "bf16"])
 @pytest.mark.parametrize("use_graph", [False, True])
-def test_solve_matches_oracle(sloppy, use_graph):
+@pytest.mark.parametrize("tc", ["0", "1"])
+def test_solve_matches_oracle(sloppy, use_graph, tc, monkeypatch):
+    """tc: MDWF_TC=0 keeps the 16-bit hops on CUDA cores, 1 puts them on the tcgen05
+    tensor-core kernel (the fused CG-iteration kernels included)."""
+    if tc == "1" and sloppy in ("f64", "f32"):
+        pytest.skip("the tensor-core hop serves 16-bit storage only")
+    monkeypatch.setenv("MDWF_TC", tc)
     m = lib()
     dims, Ls, mf = (4, 4, 4, 4), 8, 0.05
     U, Ub, p, b, xo = _problem(dims, Ls, mf)
@@ -56,7 +62,9 @@ def test_solve_host_buffers_and_ragged_lattice():
     assert rel(x, xo) <= 1e-8
 
 
-def test_solve_multi_matches_single():
+@pytest.mark.parametrize("tc", ["0", "1"])
+def test_solve_multi_matches_single(tc, monkeypatch):
+    monkeypatch.setenv("MDWF_TC", tc)
     m = lib()
     dims, Ls, mf = (4, 4, 4, 4), 6, 0.05
     U = inputs.gauge_links(dims, 0.3, 5)
