@@ -92,8 +92,19 @@ enum mdwf_op {
   MDWF_OP_MDAGM = 14,      /* out_o = M_pc^+ M_pc in_o                             */
   MDWF_OP_FULL_D = 15,     /* out = D in (both parities)                           */
   MDWF_OP_FULL_D_DAG = 16, /* out = D^+ in                                         */
-  MDWF_OP_COUNT = 17
+  MDWF_OP_MPC_SYM = 17,    /* out_o = M_sym in_o (symmetric form, see below)         */
+  MDWF_OP_MPC_SYM_DAG = 18,/* out_o = M_sym^+ in_o                                 */
+  MDWF_OP_COUNT = 19
 };
+
+/* Even-odd preconditioned forms of the odd-site system (mdwf_solve_params.pc_form).
+ * The paper names red-black preconditioning without fixing the form.
+ *   MDWF_PC_LEFT: M_pc = 1 - (1/4) A5^-1 H_oe D5 A5^-1 H_eo D5, solving M_pc x_o = b~_o.
+ *   MDWF_PC_SYM:  the symmetric form of the rescaled operator D D5^-1, whose diagonal
+ *                 block is A~ = A5 D5^-1:  M_sym = 1 - (1/4) A~^-1 H_oe A~^-1 H_eo with
+ *                 A~^-1 = D5 A5^-1 (= D5 M_pc D5^-1), solving M_sym y = D5 b~_o and
+ *                 x_o = D5^-1 y.  Its true residual is |D5 b~ - M_sym y| / |D5 b~|. */
+enum mdwf_pc_form { MDWF_PC_LEFT = 0, MDWF_PC_SYM = 1 };
 
 typedef struct mdwf_params {
   int dims[4];        /* X, Y, Z, T: each even and >= 2 */
@@ -106,6 +117,10 @@ typedef struct mdwf_params {
                          rebuild the third as conj(row0 x row1) */
   int check_su3;      /* nonzero: mdwf_load_gauge rejects links with |U U^+ - 1| or
                          |det U - 1| above 1e-9 (MDWF_ERR_NOT_SU3) */
+  int t_ranks;        /* T partitions of the global lattice (1: the context holds it all) */
+  int t_rank;         /* this context's partition: global timeslices
+                         [t_rank * dims[3], (t_rank + 1) * dims[3]); dims[3] is the LOCAL
+                         extent (even), the global one is t_ranks * dims[3] */
 } mdwf_params;
 
 typedef struct mdwf_solve_params {
@@ -121,6 +136,7 @@ typedef struct mdwf_solve_params {
   int location;        /* MDWF_HOST or MDWF_DEVICE for src / sol */
   int full_residual;   /* nonzero: also compute |b - D x| / |b| (a diagnostic: two extra
                           FP64 hops and a full-lattice FP64 pass) */
+  int pc_form;         /* MDWF_PC_LEFT or MDWF_PC_SYM */
 } mdwf_solve_params;
 
 typedef struct mdwf_solve_info {
@@ -128,7 +144,8 @@ typedef struct mdwf_solve_info {
   int iterations;          /* inner CG iterations */
   int reliable_updates;    /* reliable updates (mixed precision): x64 += x_s and the inner
                               residual restarted from res = b~ - M x64 */
-  double true_residual;    /* FP64 |b~ - M_pc x| / |b~| of the preconditioned system */
+  double true_residual;    /* FP64 relative residual of the odd-site system solved: LEFT
+                              |b~ - M_pc x_o| / |b~|, SYM |D5 b~ - M_sym y| / |D5 b~| */
   double full_residual;    /* FP64 |b - D x| / |b| (if requested, else -1) */
   double time_ms;          /* wall time of the call (host clock, stream synchronised) */
   int fp64_residuals;      /* residuals b~ - M_pc x recomputed with M_pc in FP64 (the others
@@ -138,10 +155,10 @@ typedef struct mdwf_solve_info {
 typedef struct mdwf_ctx mdwf_ctx;
 
 /* Fill *p with defaults: dims 4^4, Ls 8, b5 1.5, c5 0.5, M5 1.3, mf 0.05, t_bc -1,
- * recon 18, check_su3 1. */
+ * recon 18, check_su3 1, t_ranks 1, t_rank 0. */
 void mdwf_default_params(mdwf_params* p);
 /* Defaults: tol 1e-10, maxiter 100000, sloppy F16, delta 0.05, ru_interval 100,
- * check_interval 10, use_graph 1, location DEVICE, full_residual 0. */
+ * check_interval 10, use_graph 1, location DEVICE, full_residual 0, pc_form LEFT. */
 void mdwf_default_solve_params(mdwf_solve_params* sp);
 
 /* Create a context on the current CUDA device.  Validates the parameters
@@ -154,7 +171,9 @@ void mdwf_destroy(mdwf_ctx* ctx);
  * the context's internal SoA layout: per parity and site, the 4 forward links U_mu(x) and
  * the 4 backward links U_mu(x-mu)^+ with the boundary phase folded in.  The lower
  * precision copies are made on first use.  Returns MDWF_ERR_NOT_SU3 if check_su3 is set
- * and a link is not in SU(3). */
+ * and a link is not in SU(3).  A T-partitioned context (t_ranks > 1) takes dims[3] + 1
+ * timeslices: first the last timeslice of the partition below (global timeslice
+ * t_rank * dims[3] - 1, periodically; only its t links are read), then its own. */
 int mdwf_load_gauge(mdwf_ctx* ctx, const double* links, int where, void* stream);
 
 /* Bytes of one internal field (both parities) of precision `prec` and nrhs right-hand
@@ -250,6 +269,43 @@ long long mdwf_launch_count(const mdwf_ctx* ctx);
  * norm, BF16 48 B), links once per launch (8 per output 4D site, 18 or 12 reals), user
  * complex128 fields at 192 B per 5D site. */
 double mdwf_algorithmic_bytes(const mdwf_ctx* ctx);
+
+/* ---------------------------------------------------------------- T-partitioned lattice
+ * (Sec. "Current State of the Art": the radius-one stencil is decomposed across GPUs,
+ * faces are exchanged and the interior is computed while they travel.)  A context with
+ * t_ranks > 1 holds dims[3] timeslices of the global lattice.  Every hop it applies packs
+ * the two faces of its input half -- per site of its first and of its last timeslice
+ * and per column, the 12 reals of the half spinor (1 -/+ sig gamma_4) psi the receiving
+ * hop needs, in the compute type (double for F64, float otherwise), followed for F16 by
+ * one float norm per site and column -- launches the interior timeslices, calls the face
+ * exchange, then launches the first and last timeslices, which take their t neighbours
+ * across the boundary from the received faces.  The result is bit-identical to the
+ * undecomposed operator's.  Operators whose kernels reduce over the lattice (the CG
+ * iteration) need a global sum and are not available: mdwf_solve* return MDWF_ERR_STATE.
+ *
+ * The exchange moves `bytes` bytes: send_lo (faces of this partition's first timeslice)
+ * to the partition below, which receives it as its recv_hi; send_hi (last timeslice) to
+ * the partition above, received as recv_lo; periodic in t_rank.  It must have completed
+ * the transfers in the order of `stream` when it returns 0 (nonzero: an error status
+ * that the calling apply returns). */
+typedef int (*mdwf_face_exchange_fn)(void* user, const void* send_lo, const void* send_hi, void* recv_lo,
+                                     void* recv_hi, size_t bytes, void* stream);
+/* Set the face exchange of a partitioned context (fn NULL: none). */
+int mdwf_set_face_exchange(mdwf_ctx* ctx, mdwf_face_exchange_fn fn, void* user);
+/* Bytes of one face of precision prec and nrhs right-hand sides. */
+int mdwf_face_bytes(const mdwf_ctx* ctx, int prec, int nrhs, size_t* bytes);
+/* Use caller-owned device buffers (each at least mdwf_face_bytes for the precisions and
+ * right-hand sides applied) for the faces instead of the context's own; NULLs: back to
+ * the context's own. */
+int mdwf_set_face_buffers(mdwf_ctx* ctx, void* send_lo, void* send_hi, void* recv_lo, void* recv_hi,
+                          size_t bytes);
+/* Exchange faces among the n partitions of one lattice held by contexts of this process
+ * (ctxs[k] has t_rank k): sets each context's exchange to an in-process one that copies
+ * the neighbours' send faces into its receive buffers.  Each context must then be driven
+ * by its own host thread (one stream each), all applying the same operator at once: the
+ * exchange waits for the other partitions at a host barrier and gives up with
+ * MDWF_ERR_TIMEOUT after 60 s.  The group lives until its last context is destroyed. */
+int mdwf_group_partitions(mdwf_ctx* const* ctxs, int n);
 
 /* Name of a status code. */
 const char* mdwf_strerror(int status);

@@ -25,21 +25,26 @@ MDWF_ERR_STATE = -8
 MDWF_PREC_F64, MDWF_PREC_F32, MDWF_PREC_F16, MDWF_PREC_BF16 = 0, 1, 2, 3
 PRECS = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 MDWF_HOST, MDWF_DEVICE = 0, 1
+MDWF_PC_LEFT, MDWF_PC_SYM = 0, 1
+PC_FORMS = {"left": 0, "sym": 1}
 OPS = ["HOP_EO", "HOP_OE", "HOP_EO_DAG", "HOP_OE_DAG", "D5", "D5_DAG", "M5", "M5_DAG", "M5INV",
-       "M5INV_DAG", "HOP_EO_M5INV", "HOP_OE_M5INV", "MPC", "MPC_DAG", "MDAGM", "FULL_D", "FULL_D_DAG"]
+       "M5INV_DAG", "HOP_EO_M5INV", "HOP_OE_M5INV", "MPC", "MPC_DAG", "MDAGM", "FULL_D", "FULL_D_DAG",
+       "MPC_SYM", "MPC_SYM_DAG"]
 OP = {n: i for i, n in enumerate(OPS)}
 
 
 class mdwf_params(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int * 4), ("Ls", ctypes.c_int), ("b5", ctypes.c_double),
                 ("c5", ctypes.c_double), ("M5", ctypes.c_double), ("mf", ctypes.c_double),
-                ("t_bc", ctypes.c_double), ("gauge_recon", ctypes.c_int), ("check_su3", ctypes.c_int)]
+                ("t_bc", ctypes.c_double), ("gauge_recon", ctypes.c_int), ("check_su3", ctypes.c_int),
+                ("t_ranks", ctypes.c_int), ("t_rank", ctypes.c_int)]
 
 
 class mdwf_solve_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("sloppy_prec", ctypes.c_int),
                 ("delta", ctypes.c_double), ("ru_interval", ctypes.c_int), ("check_interval", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("location", ctypes.c_int), ("full_residual", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("location", ctypes.c_int), ("full_residual", ctypes.c_int),
+                ("pc_form", ctypes.c_int)]
 
 
 class mdwf_solve_info(ctypes.Structure):
@@ -56,6 +61,8 @@ class MdwfError(RuntimeError):
 
 _lib = None
 _V, _I, _D, _S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+# int (*)(void* user, const void* send_lo, const void* send_hi, void* recv_lo, void* recv_hi, size_t, void* stream)
+FACE_EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, _V, _V, _V, _V, _V, _S, _V)
 _SIGS = {
     "mdwf_default_params": (None, [ctypes.POINTER(mdwf_params)]),
     "mdwf_default_solve_params": (None, [ctypes.POINTER(mdwf_solve_params)]),
@@ -80,6 +87,10 @@ _SIGS = {
     "mdwf_tune_entry": (_I, [_V, _I, ctypes.c_char_p, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "mdwf_launch_count": (ctypes.c_longlong, [_V]),
     "mdwf_algorithmic_bytes": (ctypes.c_double, [_V]),
+    "mdwf_set_face_exchange": (_I, [_V, FACE_EXCHANGE_FN, _V]),
+    "mdwf_face_bytes": (_I, [_V, _I, _I, ctypes.POINTER(_S)]),
+    "mdwf_set_face_buffers": (_I, [_V, _V, _V, _V, _V, _S]),
+    "mdwf_group_partitions": (_I, [ctypes.POINTER(_V), _I]),
     "mdwf_strerror": (ctypes.c_char_p, [_I]),
     "mdwf_last_error": (ctypes.c_char_p, []),
 }
@@ -257,3 +268,24 @@ def mdwf_algorithmic_bytes(ctx):
 
 def mdwf_last_error():
     return load().mdwf_last_error().decode()
+
+
+def mdwf_set_face_exchange(ctx, fn, user=None):
+    """fn: a FACE_EXCHANGE_FN (keep a reference to it while the context uses it) or None."""
+    return _check(load().mdwf_set_face_exchange(ctx, fn if fn is not None else FACE_EXCHANGE_FN(), user))
+
+
+def mdwf_face_bytes(ctx, prec, nrhs):
+    n = ctypes.c_size_t()
+    _check(load().mdwf_face_bytes(ctx, prec, nrhs, ctypes.byref(n)))
+    return n.value
+
+
+def mdwf_set_face_buffers(ctx, send_lo, send_hi, recv_lo, recv_hi, nbytes):
+    ps = [ptr(x)[0] if x is not None else None for x in (send_lo, send_hi, recv_lo, recv_hi)]
+    return _check(load().mdwf_set_face_buffers(ctx, ps[0], ps[1], ps[2], ps[3], nbytes))
+
+
+def mdwf_group_partitions(ctxs):
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    return _check(load().mdwf_group_partitions(arr, len(ctxs)))

@@ -6,12 +6,14 @@ from . import _lib as L
 
 
 class Context:
-    def __init__(self, dims, Ls, b5=1.5, c5=0.5, M5=1.3, mf=0.05, t_bc=-1.0, recon=18, check_su3=True):
+    def __init__(self, dims, Ls, b5=1.5, c5=0.5, M5=1.3, mf=0.05, t_bc=-1.0, recon=18, check_su3=True,
+                 t_ranks=1, t_rank=0):
         p = L.mdwf_default_params()
         for i in range(4):
             p.dims[i] = int(dims[i])
         p.Ls, p.b5, p.c5, p.M5, p.mf, p.t_bc = int(Ls), b5, c5, M5, mf, t_bc
         p.gauge_recon, p.check_su3 = int(recon), int(bool(check_su3))
+        p.t_ranks, p.t_rank = int(t_ranks), int(t_rank)
         self.params = p
         self.dims = tuple(int(d) for d in dims)
         self.Ls = int(Ls)
@@ -45,11 +47,12 @@ class Context:
         return L.mdwf_field_bytes(self.h, L.PRECS.get(prec, prec), nrhs)
 
     def solve_params(self, tol=1e-10, sloppy="f16", maxiter=100000, delta=0.05, ru_interval=100, check_interval=10,
-                     use_graph=True, location=None, full_residual=False):
+                     use_graph=True, location=None, full_residual=False, pc_form="left"):
         sp = L.mdwf_default_solve_params()
         sp.tol, sp.maxiter, sp.sloppy_prec = tol, maxiter, L.PRECS.get(sloppy, sloppy)
         sp.delta, sp.ru_interval, sp.check_interval = delta, ru_interval, check_interval
         sp.use_graph, sp.full_residual = int(use_graph), int(full_residual)
+        sp.pc_form = L.PC_FORMS.get(pc_form, pc_form)
         if location is not None:
             sp.location = location
         return sp

@@ -12,6 +12,9 @@
 #include <chrono>
 #include <cmath>
 #include <complex>
+#include <condition_variable>
+#include <memory>
+#include <mutex>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -88,6 +91,13 @@ struct mdwf_ctx {
   std::map<std::string, double> graph_bytes;  // algorithmic bytes of one replay
   long long launches = 0;
   double bytes = 0.0;  // algorithmic HBM bytes of every kernel launched (see site_bytes)
+  // T partition (t_ranks > 1): the local lattice is one slab of the global one
+  long long slice_vh = 0;            // checkerboard sites of one local timeslice
+  mdwf_face_exchange_fn xfn = nullptr;
+  void* xuser = nullptr;
+  void* user_faces[4] = {};          // caller-owned face buffers (send lo/hi, recv lo/hi)
+  size_t user_face_bytes = 0;
+  std::shared_ptr<void> group;       // in-process partition group this context belongs to
 };
 
 namespace {
@@ -133,6 +143,7 @@ struct Ops {  // operators of a context at a given quark mass
   SOp D5(bool dag) const { return sop_bidiag(b5, c5, dag); }
   SOp A5(bool dag) const { return sop_bidiag(al, be, dag); }
   SOp A5inv(bool dag) const { return sop_inv(al, be, dag, Ls, mf); }
+  SOp D5inv(bool dag) const { return sop_inv(b5, c5, dag, Ls, mf); }
 };
 Ops ops_of(const mdwf_ctx* c, double mf) {
   Ops o;
@@ -404,6 +415,69 @@ std::string chain_sig(const SChain& ch) {
   return s;
 }
 
+// bytes of one face: 12 compute-type reals per face site and column, then (F16) a norm
+size_t face_bytes_of(const mdwf_ctx* c, int prec, int nrhs) {
+  const size_t W = (size_t)nrhs * c->Ls;
+  const size_t data = (size_t)c->slice_vh * W * 12 * (prec == F64 ? 8 : 4);
+  return ((data + 255) & ~(size_t)255) + (prec == F16 ? (size_t)c->slice_vh * W * 4 : 0);
+}
+
+// One hop on a T-partitioned lattice: pack the input half's two faces, launch the interior
+// timeslices, exchange, launch the first and last timeslices with their t neighbours
+// across the boundary taken from the received faces (bit-identical to one launch on the
+// undecomposed lattice: every site runs the same code on the same reals).
+int hop_partitioned(mdwf_ctx* c, int prec, bool dag, bool r12, bool epi, const HopParams& p, int cfg,
+                    const Field& in, const Field& out, cudaStream_t st) {
+  if (!c->xfn) { g_last_error = "T-partitioned context without a face exchange"; return MDWF_ERR_STATE; }
+  const long long sv = c->slice_vh, vh = c->vh;
+  const size_t fb = face_bytes_of(c, prec, in.nrhs);
+  const size_t fdata = (size_t)sv * in.nrhs * c->Ls * 12 * (prec == F64 ? 8 : 4);
+  void* buf[4];
+  if (c->user_faces[0] && c->user_face_bytes >= fb) {
+    for (int k = 0; k < 4; k++) buf[k] = c->user_faces[k];
+  } else {
+    const char* names[4] = {"face_send_lo", "face_send_hi", "face_recv_lo", "face_recv_hi"};
+    for (int k = 0; k < 4; k++) CKS(ws_get(c, names[k], fb, &buf[k]));
+  }
+  auto norm_of = [&](void* b) -> float* {
+    return prec == F16 ? (float*)((char*)b + ((fdata + 255) & ~(size_t)255)) : nullptr;
+  };
+  const int SF = dag ? -1 : 1;
+  FaceParams fp;
+  fp.in = in; fp.slice_vh = sv;
+  fp.first = 0; fp.face = buf[0]; fp.norm = norm_of(buf[0]);      // first timeslice, for the hop t+1 below
+  CK(launch_pack_face(prec, SF, fp, st));
+  fp.first = vh - sv; fp.face = buf[1]; fp.norm = norm_of(buf[1]); // last timeslice, for the hop t-1 above
+  CK(launch_pack_face(prec, -SF, fp, st));
+  c->launches += 2;
+  c->bytes += 2.0 * half_bytes(in, prec) / (double)c->g.T + 2.0 * fb;
+  const bool tc = (cfg & kTcBit) != 0;
+  auto launch = [&](long long x0, long long x1, int mode, void* face, long long base) -> int {
+    if (x1 <= x0) return MDWF_SUCCESS;
+    HopParams q = p;
+    q.ns = cfg & 0xFFFF;
+    q.status = c->dev_status;
+    q.x_begin = x0; q.x_end = x1;
+    q.face_mode = mode; q.face = face; q.face_norm = face ? norm_of(face) : nullptr; q.face_base = base;
+    cudaError_t err = tc ? launch_hop_tc(prec, dag, r12, epi, q, st)
+                         : launch_hop(prec, dag, r12, epi, (cfg & kOccBit) != 0, q, st);
+    c->launches++;
+    if (err != cudaSuccess) { set_err("launch_hop", err); return MDWF_ERR_CUDA; }
+    return MDWF_SUCCESS;
+  };
+  CKS(launch(sv, vh - sv, 0, nullptr, 0));                 // interior, while the faces travel
+  const int xs = c->xfn(c->xuser, buf[0], buf[1], buf[2], buf[3], fb, (void*)st);
+  if (xs != 0) {
+    if (g_last_error.empty()) g_last_error = "face exchange failed";
+    return xs < 0 ? xs : MDWF_ERR_CUDA;
+  }
+  CKS(launch(0, sv, 1, buf[2], vh - sv));                   // first timeslice: t-1 from below
+  CKS(launch(vh - sv, vh, 2, buf[3], 0));                   // last timeslice: t+1 from above
+  c->bytes += half_bytes(in, prec) + gauge_bytes(c, prec) + (p.has_center ? half_bytes(p.center, prec) : 0.0) +
+              (p.axpy_r ? 2.0 * half_bytes(p.raxpy, prec) : half_bytes(out, prec));
+  return MDWF_SUCCESS;
+}
+
 int hop(mdwf_ctx* c, int prec, bool dag, const Field& in, const Field& out, int pout, const Epi& e,
         Red red, cudaStream_t st, std::vector<Snap> snaps = {}) {
   const void* unused;
@@ -466,6 +540,20 @@ int hop(mdwf_ctx* c, int prec, bool dag, const Field& in, const Field& out, int 
                                  std::string(tc_only ? "tc" : "") + (e.on ? "epi" : "plain") + chain_sig(e.post) +
                                      chain_sig(e.fin) + (p.has_center ? "c" : "") + (p.axpy_r ? "a" : "") +
                                      (red.mode ? "r" : ""));
+  p.x_begin = 0;
+  p.x_end = c->vh;
+  p.bc_lo = c->prm.t_rank == 0;
+  p.bc_hi = c->prm.t_rank == c->prm.t_ranks - 1;
+  if (c->prm.t_ranks > 1) {
+    if (red.mode != RED_NONE) {
+      g_last_error = "a reduction over a T-partitioned lattice needs a global sum";
+      return MDWF_ERR_STATE;
+    }
+    int cfg = dflt;
+    auto it = c->tune.find(key);
+    if (it != c->tune.end() && std::find(cands.begin(), cands.end(), it->second.ns) != cands.end()) cfg = it->second.ns;
+    return hop_partitioned(c, prec, dag, r12, e.on, p, cfg, in, out, st);
+  }
   auto run = [&](int cfg) -> int {
     HopParams q = p;
     const int ns = cfg & 0xFFFF;
@@ -643,6 +731,43 @@ int apply_mpc_dag(mdwf_ctx* c, int prec, const Field& in, const Field& out, cuda
   return hop(c, prec, true, y, out, 1, e4, red_none(), st);
 }
 
+// M_sym in (odd) -> out (odd): M_sym = 1 - (1/4) X H_oe X H_eo, X = D5 A5^-1 (two fused
+// hop kernels, no input pre-chain)
+int apply_mpc_sym(mdwf_ctx* c, int prec, const Field& in, const Field& out, cudaStream_t st) {
+  const Ops o = ops_of(c, c->prm.mf);
+  Field w;
+  CKS(ws_half(c, "mpc_w", prec, in.nrhs, &w));
+  Epi e1;
+  e1.on = true; e1.post = chain(o.A5inv(false), o.D5(false)); e1.mf = o.mf;
+  CKS(hop(c, prec, false, in, w, 0, e1, red_none(), st));
+  Epi e2;
+  e2.on = true; e2.post = chain(o.A5inv(false), o.D5(false)); e2.hc = -0.25; e2.center = in; e2.mf = o.mf;
+  return hop(c, prec, false, w, out, 1, e2, red_none(), st);
+}
+
+// M_sym^+ = 1 - (1/4) (H^+)_oe X^+ (H^+)_eo X^+, X^+ = A5^-+ D5^+
+int apply_mpc_sym_dag(mdwf_ctx* c, int prec, const Field& in, const Field& out, cudaStream_t st) {
+  const Ops o = ops_of(c, c->prm.mf);
+  Field qt, y;
+  CKS(ws_half(c, "mpcd_q", prec, in.nrhs, &qt));
+  CKS(ws_half(c, "mpcd_y", prec, in.nrhs, &y));
+  CKS(sl_chain(c, prec, qt, in, chain(o.D5(true), o.A5inv(true)), 1.0, nullptr, 0.0, o.mf, st));
+  Epi e3;
+  e3.on = true; e3.post = chain(o.D5(true), o.A5inv(true)); e3.mf = o.mf;
+  CKS(hop(c, prec, true, qt, y, 0, e3, red_none(), st));
+  Epi e4;
+  e4.on = true; e4.hc = -0.25; e4.center = in; e4.mf = o.mf;
+  return hop(c, prec, true, y, out, 1, e4, red_none(), st);
+}
+
+// the odd-site operator of a preconditioned form and its adjoint
+int apply_M(mdwf_ctx* c, int form, int prec, const Field& in, const Field& out, cudaStream_t st) {
+  return form == MDWF_PC_SYM ? apply_mpc_sym(c, prec, in, out, st) : apply_mpc(c, prec, in, out, st);
+}
+int apply_Mdag(mdwf_ctx* c, int form, int prec, const Field& in, const Field& out, cudaStream_t st) {
+  return form == MDWF_PC_SYM ? apply_mpc_sym_dag(c, prec, in, out, st) : apply_mpc_dag(c, prec, in, out, st);
+}
+
 // full 5D D (or D^+) on both parities at quark mass mf
 int apply_full(mdwf_ctx* c, int prec, bool dag, const Field in[2], const Field out[2], double mf, cudaStream_t st) {
   const Ops o = ops_of(c, mf);
@@ -668,12 +793,12 @@ int apply_full(mdwf_ctx* c, int prec, bool dag, const Field in[2], const Field o
 
 // ---------------------------------------------------------------- CG
 struct CGSet {
-  int prec, prec_x, nrhs;
+  int prec, prec_x, nrhs, form;
   Field x, r, p, ph, w, qt, y;
 };
 
-int make_cgset(mdwf_ctx* c, int prec, int prec_x, int nrhs, CGSet* s) {
-  s->prec = prec; s->prec_x = prec_x; s->nrhs = nrhs;
+int make_cgset(mdwf_ctx* c, int prec, int prec_x, int nrhs, int form, CGSet* s) {
+  s->prec = prec; s->prec_x = prec_x; s->nrhs = nrhs; s->form = form;
   CKS(ws_half(c, "cg_x", prec_x, nrhs, &s->x));
   CKS(ws_half(c, "cg_r", prec, nrhs, &s->r));
   CKS(ws_half(c, "cg_p", prec, nrhs, &s->p));
@@ -684,8 +809,34 @@ int make_cgset(mdwf_ctx* c, int prec, int prec_x, int nrhs, CGSet* s) {
   return MDWF_SUCCESS;
 }
 
+int cg_update(mdwf_ctx* c, const CGSet& v, const SChain& ch, bool phat, cudaStream_t st);
+
+// One CG iteration on M_sym^+ M_sym (X = D5 A5^-1): K1 w_e = X H_eo p; K2 q = p - X H_oe w / 4
+// with |q|^2 -> alpha; X^+ q (s-local); K3 y_e = X^+ (H^+)_eo X^+ q; K4 r -= alpha
+// (q - (H^+)_oe y / 4) with |r|^2 -> beta; then x += alpha p, p = r + beta p.
+int cg_iteration_sym(mdwf_ctx* c, const CGSet& v, cudaStream_t st) {
+  const Ops o = ops_of(c, c->prm.mf);
+  const int P = v.prec;
+  Epi e1;
+  e1.on = true; e1.post = chain(o.A5inv(false), o.D5(false)); e1.mf = o.mf;
+  CKS(hop(c, P, false, v.p, v.w, 0, e1, red_none(), st));
+  Epi e2;
+  e2.on = true; e2.post = chain(o.A5inv(false), o.D5(false)); e2.hc = -0.25; e2.center = v.p; e2.norm_pre = true;
+  e2.mf = o.mf;
+  CKS(hop(c, P, false, v.w, v.qt, 1, e2, red_cg(c, RED_CG_ALPHA, v.nrhs), st));
+  CKS(sl_chain(c, P, v.ph, v.qt, chain(o.D5(true), o.A5inv(true)), 1.0, nullptr, 0.0, o.mf, st));
+  Epi e3;
+  e3.on = true; e3.post = chain(o.D5(true), o.A5inv(true)); e3.mf = o.mf;
+  CKS(hop(c, P, true, v.ph, v.y, 0, e3, red_none(), st));
+  Epi e4;
+  e4.on = true; e4.hc = -0.25; e4.center = v.qt; e4.raxpy = v.r; e4.mf = o.mf;
+  CKS(hop(c, P, true, v.y, v.r, 1, e4, red_cg(c, RED_CG_BETA, v.nrhs), st));
+  return cg_update(c, v, chain(), false, st);
+}
+
 // One CG iteration on M_pc^+ M_pc: five kernels, scalars stay on the device.
 int cg_iteration(mdwf_ctx* c, const CGSet& v, cudaStream_t st) {
+  if (v.form == MDWF_PC_SYM) return cg_iteration_sym(c, v, st);
   const Ops o = ops_of(c, c->prm.mf);
   const int P = v.prec;
   Epi e1;  // w_e = D5 A5^-1 H_eo phat
@@ -702,10 +853,16 @@ int cg_iteration(mdwf_ctx* c, const CGSet& v, cudaStream_t st) {
   e4.on = true; e4.post = chain(o.D5(true)); e4.hc = -0.25; e4.center = v.qt; e4.cop = chain(o.A5(true));
   e4.raxpy = v.r; e4.mf = o.mf;
   CKS(hop(c, P, true, v.y, v.r, 1, e4, red_cg(c, RED_CG_BETA, v.nrhs), st));
-  // x += alpha p ; p = r + beta p ; phat = D5 p
+  return cg_update(c, v, chain(o.D5(false)), true, st);
+}
+
+// x += alpha p ; p = r + beta p ; phat = ch(p) when phat
+int cg_update(mdwf_ctx* c, const CGSet& v, const SChain& ch, bool phat, cudaStream_t st) {
+  const Ops o = ops_of(c, c->prm.mf);
+  const int P = v.prec;
   SLParams q;
   memset(&q, 0, sizeof q);
-  q.a = v.p; q.b = v.r; q.c = v.ph; q.x = v.x; q.vh = c->vh; q.chain = chain(o.D5(false)); q.mf = o.mf;
+  q.a = v.p; q.b = v.r; q.c = phat ? v.ph : null_field(); q.x = v.x; q.vh = c->vh; q.chain = ch; q.mf = o.mf;
   q.red = red_cg(c, RED_NONE, v.nrhs);
   const int W = v.nrhs * c->Ls;
   std::vector<Snap> snaps = {{v.x.data, field_bytes_of(v.x, v.prec_x)}, {v.p.data, field_bytes_of(v.p, P)}};
@@ -716,13 +873,13 @@ int cg_iteration(mdwf_ctx* c, const CGSet& v, cudaStream_t st) {
     qq.ns = ns;
     cudaError_t err = launch_cg_update(v.prec_x, P, qq, st);
     c->launches++;
-    c->bytes += 2.0 * half_bytes(v.x, v.prec_x) + 4.0 * half_bytes(v.p, P);
+    c->bytes += 2.0 * half_bytes(v.x, v.prec_x) + (phat ? 4.0 : 3.0) * half_bytes(v.p, P);
     if (err != cudaSuccess) { set_err("launch_cg_update", err); return MDWF_ERR_CUDA; }
     return MDWF_SUCCESS;
   };
   int ns;
-  CKS(tuned_ns(c, key_of(c, "cgupd", P, v.nrhs, std::to_string(v.prec_x)), ns_candidates(W), ns_default(W), snaps,
-               st, run, &ns));
+  CKS(tuned_ns(c, key_of(c, "cgupd", P, v.nrhs, std::to_string(v.prec_x) + (phat ? "" : "n")), ns_candidates(W),
+               ns_default(W), snaps, st, run, &ns));
   return run(ns);
 }
 
@@ -755,7 +912,8 @@ int run_iterations(mdwf_ctx* c, const CGSet& v, int n, bool use_graph, cudaStrea
     return MDWF_SUCCESS;
   }
   char key[256];
-  snprintf(key, sizeof key, "%d/%d/%d/%d/%p/%p/%p", v.prec, v.prec_x, v.nrhs, n, v.r.data, v.x.data, (void*)st);
+  snprintf(key, sizeof key, "%d/%d/%d/%d/%d/%p/%p/%p", v.prec, v.prec_x, v.nrhs, v.form, n, v.r.data, v.x.data,
+           (void*)st);
   auto it = c->graphs.find(key);
   if (it == c->graphs.end()) {
     cudaGraph_t graph;
@@ -776,7 +934,7 @@ int run_iterations(mdwf_ctx* c, const CGSet& v, int n, bool use_graph, cudaStrea
     it = c->graphs.emplace(key, exec).first;
   }
   CK(cudaGraphLaunch(it->second, st));
-  c->launches += 5LL * n;
+  c->launches += (v.form == MDWF_PC_SYM ? 6LL : 5LL) * n;
   c->bytes += c->graph_bytes[key];
   return MDWF_SUCCESS;
 }
@@ -791,12 +949,12 @@ struct SolveState {
   int fp64_res = 0;               // FP64 recomputations of b~ - M x
 };
 
-// res = b~ - M_pc x (FP64), |res|^2 per rhs
-int true_residual(mdwf_ctx* c, const Field& bt, const Field& x, const Field& res, std::vector<double>& r2,
+// res = b~ - M x (FP64), |res|^2 per rhs
+int true_residual(mdwf_ctx* c, int form, const Field& bt, const Field& x, const Field& res, std::vector<double>& r2,
                   cudaStream_t st) {
   Field q;
   CKS(ws_half(c, "tr_q", F64, x.nrhs, &q));
-  CKS(apply_mpc(c, F64, x, q, st));
+  CKS(apply_M(c, form, F64, x, q, st));
   CKS(sl_axpby(c, F64, &res, bt, 1.0, &q, -1.0, red_store(c, x.nrhs), st));
   CK(cudaMemcpyAsync(c->red_host, c->red_out, x.nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -819,8 +977,9 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
   const int nrhs = bt.nrhs;
   const bool mixed = sp->sloppy_prec != F64;
   const int P = sp->sloppy_prec;
+  const int form = sp->pc_form;
   CGSet v;
-  CKS(make_cgset(c, P, mixed ? F32 : F64, nrhs, &v));
+  CKS(make_cgset(c, P, mixed ? F32 : F64, nrhs, form, &v));
   Field res, r64;
   CKS(ws_half(c, "res64", F64, nrhs, &res));
   CKS(ws_half(c, "r64", F64, nrhs, &r64));
@@ -839,19 +998,19 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
     CKS(ws_half(c, "r32", F32, nrhs, &r32));
     CKS(ws_half(c, "res32", F32, nrhs, &res32));
     CKS(sl_convert(c, F32, res32, F64, bt, false, false, st));
-    CKS(apply_mpc_dag(c, F32, res32, r32, st));
+    CKS(apply_Mdag(c, form, F32, res32, r32, st));
     CKS(norm2(c, F32, r32, g0, st));
     CKS(sl_convert(c, P, v.r, F32, r32, false, false, st));
     // FP64 residual of x64 = 0
     CK(cudaMemcpyAsync(res.data, bt.data, field_bytes_of(bt, F64), cudaMemcpyDeviceToDevice, st));
   } else {
-    CKS(apply_mpc_dag(c, F64, bt, r64, st));
+    CKS(apply_Mdag(c, form, F64, bt, r64, st));
     CKS(norm2(c, F64, r64, g0, st));
     CK(cudaMemcpyAsync(v.r.data, r64.data, field_bytes_of(r64, F64), cudaMemcpyDeviceToDevice, st));
   }
   CK(cudaMemcpyAsync(v.p.data, v.r.data, field_bytes_of(v.r, P), cudaMemcpyDeviceToDevice, st));
   if (v.r.norm) CK(cudaMemcpyAsync(v.p.norm, v.r.norm, (size_t)c->vh * nrhs * c->Ls * 4, cudaMemcpyDeviceToDevice, st));
-  CKS(sl_chain(c, P, v.ph, v.p, chain(o.D5(false)), 1.0, nullptr, 0.0, o.mf, st));
+  if (form != MDWF_PC_SYM) CKS(sl_chain(c, P, v.ph, v.p, chain(o.D5(false)), 1.0, nullptr, 0.0, o.mf, st));
 
   for (int r = 0; r < nrhs; r++) {
     if (!std::isfinite(S->bnorm2[r]) || !std::isfinite(g0[r])) {
@@ -933,7 +1092,7 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
         Field q32, q64;
         CKS(ws_half(c, "ru_q32", F32, nrhs, &q32));
         CKS(ws_half(c, "tr_q", F64, nrhs, &q64));
-        CKS(apply_mpc(c, F32, v.x, q32, st));
+        CKS(apply_M(c, form, F32, v.x, q32, st));
         CKS(sl_convert(c, F64, q64, F32, q32, false, false, st));
         CKS(sl_axpby(c, F64, &res, res, 1.0, &q64, -1.0, red_store(c, nrhs), st));
         CK(cudaMemcpyAsync(c->red_host, c->red_out, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -950,14 +1109,14 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
       }
       if (anchor) {
         if (!folded) CKS(sl_convert(c, F64, x64, F32, v.x, true, true, st));
-        CKS(true_residual(c, bt, x64, res, rr2, st));
+        CKS(true_residual(c, form, bt, x64, res, rr2, st));
         S->fp64_res++;
         ru_since_anchor = 0;
         x_fresh = true;
         anchor_r2 = rr2;
       }
     } else {
-      CKS(true_residual(c, bt, v.x, res, rr2, st));
+      CKS(true_residual(c, form, bt, v.x, res, rr2, st));
       S->fp64_res++;
       x_fresh = true;
     }
@@ -966,7 +1125,7 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
       if (mixed && !anchor && verbose_level() >= 2) {
         Field rd;
         CKS(ws_half(c, "res_dbg", F64, nrhs, &rd));
-        CKS(true_residual(c, bt, x64, rd, chk, st));
+        CKS(true_residual(c, form, bt, x64, rd, chk, st));
       }
       for (int r = 0; r < nrhs; r++) {
         if (S->done[r]) continue;
@@ -997,7 +1156,7 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
       // r = M^+ (b~ - M x) with the FP64 residual rounded to FP32 (relative precision of
       // the inner iteration is all it needs), requantised to the inner storage
       CKS(sl_convert(c, F32, res32, F64, res, false, false, st));
-      CKS(apply_mpc_dag(c, F32, res32, r32, st));
+      CKS(apply_Mdag(c, form, F32, res32, r32, st));
       std::vector<double> g, rp;
       CKS(norm2(c, F32, r32, g, st));
       CKS(sl_convert(c, P, v.r, F32, r32, false, false, st));
@@ -1015,7 +1174,7 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
         coef[r] = g[r] > 0.0 ? (g[r] - rp[r]) / g[r] : 0.0;
       }
       CKS(rhs_axpy(c, P, v.p, v.r, coef, st));
-      CKS(sl_chain(c, P, v.ph, v.p, chain(o.D5(false)), 1.0, nullptr, 0.0, o.mf, st));
+      if (form != MDWF_PC_SYM) CKS(sl_chain(c, P, v.ph, v.p, chain(o.D5(false)), 1.0, nullptr, 0.0, o.mf, st));
     }
     CKS(push_scalars(c, nrhs, st));
   }
@@ -1025,7 +1184,7 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
   if (!x_fresh) {
     if (mixed) CKS(sl_convert(c, F64, x64, F32, v.x, true, true, st));
     std::vector<double> rr2;
-    CKS(true_residual(c, bt, x64, res, rr2, st));
+    CKS(true_residual(c, form, bt, x64, res, rr2, st));
     S->fp64_res++;
     for (int r = 0; r < nrhs; r++) S->true_rel[r] = S->bnorm2[r] > 0 ? std::sqrt(rr2[r] / S->bnorm2[r]) : 0.0;
   }
@@ -1055,6 +1214,55 @@ M4 gamma_mu(int mu) {
   return g;
 }
 
+// In-process exchange among the partitions of one lattice held by contexts of this
+// process, each driven by its own host thread: publish the send faces, meet at a host
+// barrier, copy the neighbours' faces into the receive buffers on this context's
+// stream, meet again so that no partition repacks a face still being read.
+struct PartGroup;
+struct PartRank {
+  PartGroup* group;
+  int rank;
+};
+struct PartGroup {
+  int n = 0;
+  std::vector<const void*> lo, hi;
+  std::vector<PartRank> ranks;
+  std::mutex m;
+  std::condition_variable cv;
+  int waiting = 0;
+  long long generation = 0;
+  // false when the other partitions did not arrive within the limit
+  bool barrier() {
+    std::unique_lock<std::mutex> l(m);
+    const long long gen = generation;
+    if (++waiting == n) {
+      waiting = 0;
+      generation++;
+      cv.notify_all();
+      return true;
+    }
+    if (cv.wait_for(l, std::chrono::seconds(60), [&] { return generation != gen; })) return true;
+    waiting--;
+    return false;
+  }
+};
+
+int group_exchange(void* user, const void* send_lo, const void* send_hi, void* recv_lo, void* recv_hi, size_t bytes,
+                   void* stream) {
+  PartRank* r = (PartRank*)user;
+  PartGroup* g = r->group;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaStreamSynchronize(st));   // this partition's faces are packed
+  g->lo[r->rank] = send_lo;
+  g->hi[r->rank] = send_hi;
+  if (!g->barrier()) { g_last_error = "face exchange: the other partitions did not arrive"; return MDWF_ERR_TIMEOUT; }
+  CK(cudaMemcpyAsync(recv_hi, g->lo[(r->rank + 1) % g->n], bytes, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(recv_lo, g->hi[(r->rank + g->n - 1) % g->n], bytes, cudaMemcpyDeviceToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  if (!g->barrier()) { g_last_error = "face exchange: the other partitions did not arrive"; return MDWF_ERR_TIMEOUT; }
+  return MDWF_SUCCESS;
+}
+
 }  // namespace
 
 // ======================================================================== C ABI
@@ -1065,6 +1273,7 @@ void mdwf_default_params(mdwf_params* p) {
   p->dims[0] = p->dims[1] = p->dims[2] = p->dims[3] = 4;
   p->Ls = 8; p->b5 = 1.5; p->c5 = 0.5; p->M5 = 1.3; p->mf = 0.05; p->t_bc = -1.0;
   p->gauge_recon = 18; p->check_su3 = 1;
+  p->t_ranks = 1; p->t_rank = 0;
 }
 
 void mdwf_default_solve_params(mdwf_solve_params* sp) {
@@ -1072,6 +1281,7 @@ void mdwf_default_solve_params(mdwf_solve_params* sp) {
   sp->tol = 1e-10; sp->maxiter = 100000; sp->sloppy_prec = MDWF_PREC_F16; sp->delta = 0.05;
   sp->ru_interval = 100; sp->check_interval = 10; sp->use_graph = 1; sp->location = MDWF_DEVICE;
   sp->full_residual = 0;
+  sp->pc_form = MDWF_PC_LEFT;
 }
 
 const char* mdwf_strerror(int s) {
@@ -1099,6 +1309,7 @@ int mdwf_create(const mdwf_params* p, mdwf_ctx** out) {
   if (p->Ls < 2 || p->Ls > MAXLS) { g_last_error = "Ls out of range [2, 32]"; return MDWF_ERR_ARG; }
   if (p->gauge_recon != 18 && p->gauge_recon != 12) { g_last_error = "gauge_recon must be 18 or 12"; return MDWF_ERR_ARG; }
   if (p->gauge_recon == 12 && std::fabs(p->t_bc) != 1.0) { g_last_error = "recon 12 needs t_bc = +-1"; return MDWF_ERR_ARG; }
+  if (p->t_ranks < 1 || p->t_rank < 0 || p->t_rank >= p->t_ranks) { g_last_error = "bad t_ranks / t_rank"; return MDWF_ERR_ARG; }
   if (!(p->mf >= 0.0) || !std::isfinite(p->b5) || !std::isfinite(p->c5) || !std::isfinite(p->M5)) {
     g_last_error = "bad Moebius parameters"; return MDWF_ERR_ARG;
   }
@@ -1118,6 +1329,7 @@ int mdwf_create(const mdwf_params* p, mdwf_ctx** out) {
   c->g.Xh = p->dims[0] / 2;
   c->vh = (long long)p->dims[0] * p->dims[1] * p->dims[2] * p->dims[3] / 2;
   c->g.vh = c->vh;
+  c->slice_vh = (long long)p->dims[0] * p->dims[1] * p->dims[2] / 2;
   c->Ls = p->Ls;
   c->alpha5 = al;
   c->beta5 = (4.0 - p->M5) * p->c5 - 1.0;
@@ -1166,7 +1378,8 @@ int mdwf_load_gauge(mdwf_ctx* c, const double* links, int where, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   CKS(ensure_small(c));
   const long long V = 2 * c->vh;
-  const size_t ubytes = (size_t)V * 4 * 9 * 16;
+  const bool ghost = c->prm.t_ranks > 1;   // a leading timeslice from the partition below
+  const size_t ubytes = (size_t)(V + (ghost ? 2 * c->slice_vh : 0)) * 4 * 9 * 16;
   const double* dev = links;
   if (where == MDWF_HOST) {
     void* p;
@@ -1188,6 +1401,9 @@ int mdwf_load_gauge(mdwf_ctx* c, const double* links, int where, void* stream) {
   GaugeParams gp;
   gp.g = c->g; gp.user = dev; gp.out64[0] = (double*)c->gauge[F64][0]; gp.out64[1] = (double*)c->gauge[F64][1];
   gp.gs = gs; gp.t_bc = c->prm.t_bc; gp.err = (c->prm.check_su3 || gs == 12) ? (double*)errp : nullptr;
+  gp.ghost = ghost ? 1 : 0;
+  gp.bc_lo = c->prm.t_rank == 0;
+  gp.bc_hi = c->prm.t_rank == c->prm.t_ranks - 1;
   CK(launch_gauge_load(gp, st));
   c->launches++;
   double err = 0.0;
@@ -1283,6 +1499,8 @@ int mdwf_apply(mdwf_ctx* c, int op, int prec, const void* in, void* out, int nrh
       CKS(apply_mpc(c, prec, fi[1], t, st));
       return apply_mpc_dag(c, prec, t, fo[1], st);
     }
+    case MDWF_OP_MPC_SYM: return apply_mpc_sym(c, prec, fi[1], fo[1], st);
+    case MDWF_OP_MPC_SYM_DAG: return apply_mpc_sym_dag(c, prec, fi[1], fo[1], st);
     case MDWF_OP_FULL_D: return apply_full(c, prec, false, fi, fo, c->prm.mf, st);
     case MDWF_OP_FULL_D_DAG: return apply_full(c, prec, true, fi, fo, c->prm.mf, st);
   }
@@ -1297,10 +1515,14 @@ int mdwf_solve_multi(mdwf_ctx* c, int nrhs, const double* src, double* sol, cons
   CKS(check_nrhs(c, nrhs));
   if (sp->sloppy_prec < 0 || sp->sloppy_prec > 3 || !(sp->tol > 0.0) || sp->maxiter < 1 ||
       (sp->location != MDWF_HOST && sp->location != MDWF_DEVICE) || !(sp->delta > 0.0 && sp->delta < 1.0) ||
-      sp->ru_interval < 1) {
+      sp->ru_interval < 1 || (sp->pc_form != MDWF_PC_LEFT && sp->pc_form != MDWF_PC_SYM)) {
     g_last_error = "bad solve parameters"; return MDWF_ERR_ARG;
   }
   if (!c->gauge_loaded) { g_last_error = "no gauge field loaded"; return MDWF_ERR_STATE; }
+  if (c->prm.t_ranks > 1) {
+    g_last_error = "CG on a T-partitioned lattice needs global sums; solve on an undecomposed context";
+    return MDWF_ERR_STATE;
+  }
   CKS(ensure_small(c));
   cudaStream_t st = (cudaStream_t)stream;
   const size_t ubytes = (size_t)nrhs * c->Ls * 2 * c->vh * 12 * 16;
@@ -1334,10 +1556,21 @@ int mdwf_solve_multi(mdwf_ctx* c, int nrhs, const double* src, double* sol, cons
     CKS(hop(c, F64, false, te, bt, 1, e, red_none(), st));
   }
   SolveState S;
-  const int cgs = cg_solve(c, bt, xo, sp, &S, st);
+  const bool sym = sp->pc_form == MDWF_PC_SYM;
+  Field rhs = bt;
+  if (sym) {   // the symmetric form solves M_sym y = D5 b~_o
+    CKS(ws_half(c, "btsym", F64, nrhs, &rhs));
+    CKS(sl_chain(c, F64, rhs, bt, chain(o.D5(false)), 1.0, nullptr, 0.0, o.mf, st));
+  }
+  const int cgs = cg_solve(c, rhs, xo, sp, &S, st);
   if (cgs != MDWF_SUCCESS && cgs != MDWF_ERR_NOT_CONVERGED) return cgs;
-  // reconstruct x_e = A5^-1 (b_e + H_eo D5 x_o / 2)
-  CKS(sl_chain(c, F64, te, xo, chain(o.D5(false)), 1.0, nullptr, 0.0, o.mf, st));
+  // reconstruct x_e = A5^-1 (b_e + H_eo D5 x_o / 2); te = D5 x_o
+  if (sym) {   // xo holds y = D5 x_o: te = y, x_o = D5^-1 y
+    CK(cudaMemcpyAsync(te.data, xo.data, field_bytes_of(xo, F64), cudaMemcpyDeviceToDevice, st));
+    CKS(sl_chain(c, F64, xo, te, chain(o.D5inv(false)), 1.0, nullptr, 0.0, o.mf, st));
+  } else {
+    CKS(sl_chain(c, F64, te, xo, chain(o.D5(false)), 1.0, nullptr, 0.0, o.mf, st));
+  }
   {
     Epi e;
     e.on = true; e.hc = 0.5; e.center = b[0]; e.fin = chain(o.A5inv(false)); e.mf = o.mf;
@@ -1515,6 +1748,60 @@ int mdwf_tune_entry(const mdwf_ctx* c, int i, char* key, int keylen, int* ns, do
 }
 
 long long mdwf_launch_count(const mdwf_ctx* c) { return c ? c->launches : 0; }
+
+int mdwf_set_face_exchange(mdwf_ctx* c, mdwf_face_exchange_fn fn, void* user) {
+  if (!c) { g_last_error = "null context"; return MDWF_ERR_ARG; }
+  c->xfn = fn;
+  c->xuser = user;
+  return MDWF_SUCCESS;
+}
+
+int mdwf_face_bytes(const mdwf_ctx* c, int prec, int nrhs, size_t* bytes) {
+  if (!c || !bytes || prec < 0 || prec > 3 || nrhs < 1) { g_last_error = "bad argument"; return MDWF_ERR_ARG; }
+  *bytes = face_bytes_of(c, prec, nrhs);
+  return MDWF_SUCCESS;
+}
+
+int mdwf_set_face_buffers(mdwf_ctx* c, void* send_lo, void* send_hi, void* recv_lo, void* recv_hi, size_t bytes) {
+  if (!c) { g_last_error = "null context"; return MDWF_ERR_ARG; }
+  const bool none = !send_lo && !send_hi && !recv_lo && !recv_hi;
+  if (!none && (!send_lo || !send_hi || !recv_lo || !recv_hi || bytes == 0)) {
+    g_last_error = "face buffers: all four or none";
+    return MDWF_ERR_ARG;
+  }
+  c->user_faces[0] = send_lo; c->user_faces[1] = send_hi;
+  c->user_faces[2] = recv_lo; c->user_faces[3] = recv_hi;
+  c->user_face_bytes = none ? 0 : bytes;
+  return MDWF_SUCCESS;
+}
+
+int mdwf_group_partitions(mdwf_ctx* const* ctxs, int n) {
+  if (!ctxs || n < 1) { g_last_error = "bad argument"; return MDWF_ERR_ARG; }
+  for (int k = 0; k < n; k++) {
+    if (!ctxs[k] || ctxs[k]->prm.t_ranks != n || ctxs[k]->prm.t_rank != k) {
+      g_last_error = "ctxs[k] must be partition k of n";
+      return MDWF_ERR_ARG;
+    }
+    for (int i = 0; i < 4; i++)
+      if (ctxs[k]->prm.dims[i] != ctxs[0]->prm.dims[i] || ctxs[k]->Ls != ctxs[0]->Ls) {
+        g_last_error = "partitions of one lattice have the same local shape";
+        return MDWF_ERR_ARG;
+      }
+  }
+  auto g = std::make_shared<PartGroup>();
+  g->n = n;
+  g->lo.assign(n, nullptr);
+  g->hi.assign(n, nullptr);
+  g->ranks.resize(n);
+  for (int k = 0; k < n; k++) {
+    g->ranks[k].group = g.get();
+    g->ranks[k].rank = k;
+    ctxs[k]->group = g;
+    ctxs[k]->xfn = group_exchange;
+    ctxs[k]->xuser = &g->ranks[k];
+  }
+  return MDWF_SUCCESS;
+}
 
 double mdwf_algorithmic_bytes(const mdwf_ctx* c) { return c ? c->bytes : 0.0; }
 

@@ -238,6 +238,23 @@ __device__ __forceinline__ typename PT<P>::C load_proj(const Field& f, unsigned 
   }
 }
 
+// The projected half spinor of a neighbour across the partition boundary, read from the
+// face the neighbouring partition packed (pack_face_kernel: the same 12 reals load_proj
+// forms, and for F16 the neighbour's norm).  nbr is the neighbour's index in the local
+// lattice with periodic wrap, i.e. face_base + the face site.
+template <int P>
+__device__ __forceinline__ typename PT<P>::C load_face(const HopParams& p, unsigned nbr, int col,
+                                                       typename PT<P>::C h[12]) {
+  using C = typename PT<P>::C;
+  const long long W = p.in.W();
+  const long long f = ((long long)nbr - p.face_base) * W + col;
+  const C* src = (const C*)p.face + f * 12;
+#pragma unroll
+  for (int k = 0; k < 12; k++) h[k] = src[k];
+  if constexpr (P == F16) return p.face_norm[f];
+  return (C)1;
+}
+
 // Link staging stride in shared memory (compute-precision reals per link, 16-byte rows)
 template <typename C> __host__ __device__ constexpr int link_stride() { return sizeof(C) == 8 ? 18 : 20; }
 
@@ -254,9 +271,9 @@ hop_kernel(const __grid_constant__ HopParams p) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int site_l = tid / W;
   const int col = tid - site_l * W;
-  const long long site0 = (long long)blockIdx.x * p.ns;
+  const long long site0 = p.x_begin + (long long)blockIdx.x * p.ns;
   const long long x_cb = site0 + site_l;
-  const bool active = x_cb < p.g.vh;
+  const bool active = x_cb < p.x_end;
   constexpr int SF = DAG ? -1 : 1;
   constexpr int LSTR = link_stride<C>();
   // shared: links of the CTA's sites (compute precision), neighbour table, epilogue
@@ -268,13 +285,14 @@ hop_kernel(const __grid_constant__ HopParams p) {
   // neighbour; forward links carry the boundary phase on t at T-1, backward ones on t at 0
   for (int i = tid; i < p.ns * 8; i += nt) {
     const long long x = site0 + (i >> 3);
-    if (x >= p.g.vh) continue;
+    if (x >= p.x_end) continue;
     const int d = i & 7, mu = d & 3;
     int c[4];
     cb_coords(p.g, x, p.pout, c);
     snbr[i] = (unsigned)nbr_cb(p.g, c, mu, d < 4 ? +1 : -1);
     C U[18];
-    const bool flip = R12 && mu == 3 && p.t_bc < 0 && (d < 4 ? c[3] == p.g.T - 1 : c[3] == 0);
+    const bool flip = R12 && mu == 3 && p.t_bc < 0 &&
+                      (d < 4 ? c[3] == p.g.T - 1 && p.bc_hi : c[3] == 0 && p.bc_lo);
     load_link<P, R12>(p.gauge, (x * 8 + d) * p.gs, U, flip);
 #pragma unroll
     for (int k = 0; k < 18; k++) slink[i * LSTR + k] = U[k];
@@ -288,8 +306,9 @@ hop_kernel(const __grid_constant__ HopParams p) {
     const unsigned* nb = snbr + site_l * 8;
     const C* lk = slink + site_l * 8 * LSTR;
     C h[12];
-#define HOP_D(D, MU, SIG)                                                 \
-    { const C nrm = load_proj<P, MU, SIG>(p.in, nb[D], col, h);           \
+#define HOP_D(D, MU, SIG)                                                                 \
+    { const C nrm = ((D) == 7 && p.face_mode == 1) || ((D) == 3 && p.face_mode == 2)         \
+                        ? load_face<P>(p, nb[D], col, h) : load_proj<P, MU, SIG>(p.in, nb[D], col, h); \
       su3_recon<MU, SIG>(h, lk + (D) * LSTR, acc, nrm); }
     HOP_D(0, 0, SF) HOP_D(4, 0, -SF) HOP_D(1, 1, SF) HOP_D(5, 1, -SF)
     HOP_D(2, 2, SF) HOP_D(6, 2, -SF) HOP_D(3, 3, SF) HOP_D(7, 3, -SF)
@@ -331,7 +350,7 @@ static cudaError_t launch_one(const HopParams& p, int threads, size_t smem, cuda
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  const long long blocks = (p.g.vh + p.ns - 1) / p.ns;
+  const long long blocks = (p.x_end - p.x_begin + p.ns - 1) / p.ns;
   HopParams q = p;   // scalars rounded once for the 32-bit kernels
   q.hcf = (float)p.hc; q.ccf = (float)p.cc; q.mff = (float)p.mf;
   hop_kernel<P, DAG, R12, EPI, OCC><<<(unsigned)blocks, threads, smem, st>>>(q);

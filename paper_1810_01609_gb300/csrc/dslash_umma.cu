@@ -61,8 +61,8 @@ __host__ __device__ inline UmLayout um_layout(int S, int nrhs, int Ls) {
   L.npad = um_npad(W);
   L.tcols = um_tcols(S * L.npad);
   L.bar = 0;                                   // mbarrier (8 B) + TMEM address (4 B)
-  L.nbr = 16;                                  // S * 8 neighbour indices
-  L.nmax = L.nbr + ((S * 8 * 4 + 15) & ~15);   // S * npad column scales (F16)
+  L.nbr = 16;                                  // S * 8 neighbour indices, then S * 8 flags
+  L.nmax = L.nbr + ((S * 8 * 5 + 15) & ~15);   // S * npad column scales (F16)
   L.a = (L.nmax + S * L.npad * 4 + 127) & ~127;
   L.b = L.a + 3 * S * UM_GRP;
   L.tile = L.b + S * (L.npad / 8) * UM_GRP;
@@ -180,58 +180,47 @@ __device__ __forceinline__ void link_row(const void* gauge, long long off, int a
   }
 }
 
-// Write the 8 rows o = 8a + 2 sigma + reim of A_x for direction d (K entries 12d..12d+11:
-// slot 0 colours 0..2, slot 1 colours 0..2, each a (re, im) pair).  sg = +-1: the sign of
-// the direction's projector (1 - sg gamma_mu).
-template <int MU>
-__device__ __forceinline__ void write_a_rows(unsigned char* A, int j, int d, int a, int sg, const uint32_t row[3]) {
-  uint32_t P0[3], P1[3], N0[3], N1[3];
+// Row o = 8a + 2 sigma + reim of A_x for direction d (K entries 12d..12d+11: slot 0
+// colours 0..2, slot 1 colours 0..2, each a (re, im) pair), from row a of the link; sg =
+// +-1 is the sign of the direction's projector (1 - sg gamma_mu).  Upper spins sigma = 0, 1
+// take U h of slot sigma; the lower spins take U h of one slot times +-1 or +-i:
+//   mu:        0     1     2     3
+//   sigma 2: (1,+i) (1,+1) (0,+i) (0,-1)      (slot, coefficient for sg = +1;
+//   sigma 3: (0,+i) (0,-1) (1,-i) (1,-1)       sg = -1 negates the coefficient)
+// A coefficient c times U h in real form: Re(c U h) and Im(c U h) are rows of the pairs
+// P0 = (Re U, -Im U), P1 = (Im U, Re U) and their negatives N0, N1:
+//   c = +1: (P0, P1), -1: (N0, N1), +i: (N1, P0), -i: (P1, N0)   for (re, im) rows.
+__device__ __forceinline__ void write_a_row(unsigned char* A, int j, int d, int o, int sg, const uint32_t row[3]) {
+  const int mu = d & 3, sigma = (o >> 1) & 3, reim = o & 1;
+  int slot, code;                     // code 0: +1, 1: -1, 2: +i, 3: -i
+  if (sigma < 2) {
+    slot = sigma;
+    code = 0;
+  } else {
+    const int t = (sigma - 2) * 4 + mu;
+    slot = (0xC3 >> t) & 1;           // sigma 2: 1 1 0 0, sigma 3: 0 0 1 1
+    code = (int)((0x7662u >> (2 * t)) & 3u);   // sigma 2: 2 0 2 1, sigma 3: 2 1 3 1
+    if (sg < 0) code ^= 1;
+  }
+  // variant: 0 P0, 1 P1, 2 N0, 3 N1 for (code, reim)
+  const int var = (int)((0x93E4u >> (4 * code + 2 * reim)) & 3u);
+  uint32_t v[6];
 #pragma unroll
   for (int b = 0; b < 3; b++) {
-    P0[b] = row[b] ^ 0x80000000u;          // (Re U, -Im U): real part of U h
-    P1[b] = swp(row[b]);                   // (Im U,  Re U): imaginary part
-    N0[b] = P0[b] ^ 0x80008000u;
-    N1[b] = P1[b] ^ 0x80008000u;
+    uint32_t w = (var & 1) ? swp(row[b]) : (row[b] ^ 0x80000000u);
+    if (var & 2) w ^= 0x80008000u;
+    v[b] = slot == 0 ? w : 0u;
+    v[3 + b] = slot == 1 ? w : 0u;
   }
-  // lower spins: (slot, coefficient) of lower0 / lower1 for +sg (code 0: +1, 1: -1,
-  // 2: +i, 3: -i); -sg flips the sign (code ^ 1)
-  constexpr int l0_slot = MU == 0 ? 1 : MU == 1 ? 1 : 0;
-  constexpr int l0_code = MU == 0 ? 2 : MU == 1 ? 0 : MU == 2 ? 2 : 1;
-  constexpr int l1_slot = MU == 0 ? 0 : MU == 1 ? 0 : 1;
-  constexpr int l1_code = MU == 0 ? 2 : MU == 1 ? 1 : MU == 2 ? 3 : 1;
-  const int flipc = sg < 0 ? 1 : 0;
-#pragma unroll
-  for (int sigma = 0; sigma < 4; sigma++) {
-    int slot, code;
-    if (sigma < 2) { slot = sigma; code = 0; }
-    else if (sigma == 2) { slot = l0_slot; code = l0_code ^ flipc; }
-    else { slot = l1_slot; code = l1_code ^ flipc; }
-#pragma unroll
-    for (int reim = 0; reim < 2; reim++) {
-      // (re row, im row) per coefficient: +1 (P0, P1), -1 (N0, N1), +i (N1, P0), -i (P1, N0)
-      const uint32_t* src;
-      if (code == 0) src = reim ? P1 : P0;
-      else if (code == 1) src = reim ? N1 : N0;
-      else if (code == 2) src = reim ? P0 : N1;
-      else src = reim ? N0 : P1;
-      uint32_t v[6];
-#pragma unroll
-      for (int b = 0; b < 3; b++) {
-        v[b] = slot == 0 ? src[b] : 0u;
-        v[3 + b] = slot == 1 ? src[b] : 0u;
-      }
-      const int grow = 24 * j + 8 * a + 2 * sigma + reim;
-      unsigned char* rowp = A + (grow >> 3) * UM_GRP + (grow & 7) * 16;
-      const int k0 = 12 * d;                 // first K element of this direction
-      const int c0 = k0 >> 3;
-      if ((d & 1) == 0) {                    // chunk c0 elements 0..7, chunk c0+1 elements 0..3
-        *(uint4*)(rowp + c0 * 128) = make_uint4(v[0], v[1], v[2], v[3]);
-        *(uint2*)(rowp + (c0 + 1) * 128) = make_uint2(v[4], v[5]);
-      } else {                               // chunk c0 elements 4..7, chunk c0+1 elements 0..7
-        *(uint2*)(rowp + c0 * 128 + 8) = make_uint2(v[0], v[1]);
-        *(uint4*)(rowp + (c0 + 1) * 128) = make_uint4(v[2], v[3], v[4], v[5]);
-      }
-    }
+  const int grow = 24 * j + o;
+  unsigned char* rowp = A + (grow >> 3) * UM_GRP + (grow & 7) * 16;
+  const int c0 = (12 * d) >> 3;       // core matrix of the direction's first K element
+  if ((d & 1) == 0) {                 // chunk c0 elements 0..7, chunk c0+1 elements 0..3
+    *(uint4*)(rowp + c0 * 128) = make_uint4(v[0], v[1], v[2], v[3]);
+    *(uint2*)(rowp + (c0 + 1) * 128) = make_uint2(v[4], v[5]);
+  } else {                            // chunk c0 elements 4..7, chunk c0+1 elements 0..7
+    *(uint2*)(rowp + c0 * 128 + 8) = make_uint2(v[0], v[1]);
+    *(uint4*)(rowp + (c0 + 1) * 128) = make_uint4(v[2], v[3], v[4], v[5]);
   }
 }
 
@@ -263,10 +252,26 @@ __device__ __forceinline__ void proj(const uint4 q[3], uint32_t h[6]) {
   }
 }
 
+// direction D's projected half spinor comes from the partition face in this launch
+template <int D>
+__device__ __forceinline__ bool from_face(const HopParams& p) {
+  return (D == 7 && p.face_mode == 1) || (D == 3 && p.face_mode == 2);
+}
+
 template <int P, int D, int SF>
-__device__ __forceinline__ void proj_dir(const Field& f, unsigned nbr, int col, uint32_t h[6]) {
+__device__ __forceinline__ void proj_dir(const HopParams& p, unsigned nbr, int col, uint32_t h[6]) {
   constexpr int MU = D & 3;
   constexpr int SIG = D < 4 ? SF : -SF;
+  const Field& f = p.in;
+  if ((D & 3) == 3 && from_face<D>(p)) {   // the 12 reals the neighbouring partition formed
+    const float* src = (const float*)p.face + (((long long)nbr - p.face_base) * f.W() + col) * 12;
+#pragma unroll
+    for (int co = 0; co < 3; co++) {
+      h[co] = pk<P>(src[2 * co], src[2 * co + 1]);
+      h[3 + co] = pk<P>(src[6 + 2 * co], src[7 + 2 * co]);
+    }
+    return;
+  }
   const uint4* dp = (const uint4*)f.data;
   const unsigned W = (unsigned)f.W();
   uint4 q[3];
@@ -275,16 +280,23 @@ __device__ __forceinline__ void proj_dir(const Field& f, unsigned nbr, int col, 
   proj<P, MU, SIG>(q, h);
 }
 
+// the F16 norm of neighbour d's column (from the face across a partition boundary)
+template <int D>
+__device__ __forceinline__ float nbr_norm(const HopParams& p, unsigned nbr, int col) {
+  const long long W = p.in.W();
+  if ((D & 3) == 3 && from_face<D>(p)) return p.face_norm[((long long)nbr - p.face_base) * W + col];
+  return __ldg(p.in.norm + nbr * W + col);
+}
+
 template <int P, int PQ, int SF>
 __device__ __forceinline__ void build_pair(const HopParams& p, const unsigned* nb, int col, float inv_nmax,
                                            unsigned char* Bcol) {
   uint32_t h0[6], h1[6];
-  proj_dir<P, 2 * PQ, SF>(p.in, nb[2 * PQ], col, h0);
-  proj_dir<P, 2 * PQ + 1, SF>(p.in, nb[2 * PQ + 1], col, h1);
+  proj_dir<P, 2 * PQ, SF>(p, nb[2 * PQ], col, h0);
+  proj_dir<P, 2 * PQ + 1, SF>(p, nb[2 * PQ + 1], col, h1);
   if constexpr (P == F16) {
-    const unsigned W = (unsigned)p.in.W();
-    const float r0 = __ldg(p.in.norm + nb[2 * PQ] * W + col) * inv_nmax;
-    const float r1 = __ldg(p.in.norm + nb[2 * PQ + 1] * W + col) * inv_nmax;
+    const float r0 = nbr_norm<2 * PQ>(p, nb[2 * PQ], col) * inv_nmax;
+    const float r1 = nbr_norm<2 * PQ + 1>(p, nb[2 * PQ + 1], col) * inv_nmax;
     const uint32_t s0 = pk<P>(r0, r0), s1 = pk<P>(r1, r1);
 #pragma unroll
     for (int i = 0; i < 6; i++) { h0[i] = hmul<P>(h0[i], s0); h1[i] = hmul<P>(h1[i], s1); }
@@ -302,8 +314,8 @@ __global__ void __launch_bounds__(UM_THREADS) hop_umma_kernel(const __grid_const
   const int S = p.ns;
   const UmLayout L = um_layout(S, nrhs, Ls);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const long long site0 = (long long)blockIdx.x * S;
-  const int nact = (int)min((long long)S, p.g.vh - site0);   // active sites of this CTA
+  const long long site0 = p.x_begin + (long long)blockIdx.x * S;
+  const int nact = (int)min((long long)S, p.x_end - site0);   // active sites of this CTA
   constexpr int SF = DAG ? -1 : 1;
   uint64_t* bar = (uint64_t*)(smem + L.bar);
   uint32_t* tslot = (uint32_t*)(smem + L.bar + 8);
@@ -322,26 +334,26 @@ __global__ void __launch_bounds__(UM_THREADS) hop_umma_kernel(const __grid_const
     asm volatile("fence.mbarrier_init.release.cluster;\n");
   }
 
-  // phase 0: neighbour table and link matrices, one thread per (site, direction, colour row)
-  for (int i = tid; i < nact * 24; i += UM_THREADS) {
-    const int j = i / 24, r = i - j * 24, d = r / 3, a = r - d * 3;
-    const long long x = site0 + j;
+  // phase 0: neighbour table (and the 12-real links' time-boundary flags), one thread
+  // per (site, direction)
+  unsigned char* sflip = smem + L.nbr + S * 8 * 4;
+  for (int i = tid; i < nact * 8; i += UM_THREADS) {
+    const int j = i >> 3, d = i & 7, mu = d & 3;
     int c[4];
-    cb_coords(p.g, x, p.pout, c);
-    const int mu = d & 3;
-    if (a == 0) snbr[j * 8 + d] = (unsigned)nbr_cb(p.g, c, mu, d < 4 ? +1 : -1);
-    const bool flip = R12 && mu == 3 && p.t_bc < 0 && (d < 4 ? c[3] == p.g.T - 1 : c[3] == 0);
-    uint32_t row[3];
-    link_row<P, R12>(p.gauge, (x * 8 + d) * p.gs, a, flip, row);
-    const int sg = d < 4 ? SF : -SF;
-    switch (mu) {
-      case 0: write_a_rows<0>(A, j, d, a, sg, row); break;
-      case 1: write_a_rows<1>(A, j, d, a, sg, row); break;
-      case 2: write_a_rows<2>(A, j, d, a, sg, row); break;
-      default: write_a_rows<3>(A, j, d, a, sg, row); break;
-    }
+    cb_coords(p.g, site0 + j, p.pout, c);
+    snbr[i] = (unsigned)nbr_cb(p.g, c, mu, d < 4 ? +1 : -1);
+    sflip[i] = R12 && mu == 3 && p.t_bc < 0 && (d < 4 ? c[3] == p.g.T - 1 && p.bc_hi : c[3] == 0 && p.bc_lo);
   }
   __syncthreads();
+
+  // link matrices, one thread per (site, direction, output row): consecutive threads
+  // write consecutive rows, i.e. distinct 16-byte bank groups of a core matrix
+  for (int i = tid; i < nact * 192; i += UM_THREADS) {
+    const int j = i / 192, rem = i - j * 192, d = rem / 24, o = rem - d * 24;
+    uint32_t row[3];
+    link_row<P, R12>(p.gauge, ((site0 + j) * 8 + d) * p.gs, o >> 3, sflip[j * 8 + d] != 0, row);
+    write_a_row(A, j, d, o, d < 4 ? SF : -SF, row);
+  }
 
   // phase 1: projected neighbours (B operand), one thread per (site, direction pair, column)
   for (int i = tid; i < nact * 4 * W; i += UM_THREADS) {
@@ -349,10 +361,10 @@ __global__ void __launch_bounds__(UM_THREADS) hop_umma_kernel(const __grid_const
     const unsigned* nb = snbr + j * 8;
     float inv = 1.0f;
     if constexpr (P == F16) {
-      const unsigned Wu = (unsigned)W;
-      float m = 0.0f;
-#pragma unroll
-      for (int d = 0; d < 8; d++) m = fmaxf(m, __ldg(p.in.norm + nb[d] * Wu + n));
+      float m = fmaxf(fmaxf(fmaxf(nbr_norm<0>(p, nb[0], n), nbr_norm<1>(p, nb[1], n)),
+                            fmaxf(nbr_norm<2>(p, nb[2], n), nbr_norm<3>(p, nb[3], n))),
+                      fmaxf(fmaxf(nbr_norm<4>(p, nb[4], n), nbr_norm<5>(p, nb[5], n)),
+                            fmaxf(nbr_norm<6>(p, nb[6], n), nbr_norm<7>(p, nb[7], n))));
       inv = m > 0.0f ? 1.0f / m : 0.0f;
       if (pq == 0) nmax[j * L.npad + n] = m;
     }
@@ -452,7 +464,7 @@ cudaError_t launch_um(const HopParams& p, size_t smem, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  const long long blocks = (p.g.vh + p.ns - 1) / p.ns;
+  const long long blocks = (p.x_end - p.x_begin + p.ns - 1) / p.ns;
   HopParams q = p;
   q.hcf = (float)p.hc; q.ccf = (float)p.cc; q.mff = (float)p.mf;
   hop_umma_kernel<P, DAG, R12, EPI><<<(unsigned)blocks, UM_THREADS, smem, st>>>(q);

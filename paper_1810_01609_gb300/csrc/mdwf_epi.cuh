@@ -154,7 +154,7 @@ __device__ __forceinline__ void hop_epilogue(const HopParams& p, typename PT<P>:
   const int Ls = p.in.Ls, nrhs = p.in.nrhs, W = Ls * nrhs;
   const int GS = tile_gstr(Ls);
   const int tid = threadIdx.x, nt = blockDim.x;
-  const long long site0 = (long long)blockIdx.x * ns;
+  const long long site0 = p.x_begin + (long long)blockIdx.x * ns;
   const int nsites = ns * W;
   const C mf = pick<C>(p.mff, p.mf), hc = pick<C>(p.hcf, p.hc), cc = pick<C>(p.ccf, p.cc);
   const bool has_post = p.post.op[0].kind != SOP_NONE;
@@ -169,7 +169,7 @@ __device__ __forceinline__ void hop_epilogue(const HopParams& p, typename PT<P>:
       const int j = lowerh ? it2 - nhalf : it2;
       const int g = j / 12, q = j - g * 12;                         // q: colour (q / 4), spin pair, re/im
       const int comp = 8 * (q >> 2) + 4 * lowerh + (q & 3);
-      if (site0 + (nrhs == 1 ? g : g / nrhs) >= p.g.vh) continue;
+      if (site0 + (nrhs == 1 ? g : g / nrhs) >= p.x_end) continue;
       chain_apply_fast(p.post, comp, tileH + g * GS + comp, TSTR, Ls, mf);
     }
     __syncthreads();
@@ -180,7 +180,7 @@ __device__ __forceinline__ void hop_epilogue(const HopParams& p, typename PT<P>:
     const int r = col / Ls, s = col - r * Ls, grp = site_l * nrhs + r;
     const long long x = site0 + site_l;
     double part = 0.0;
-    if (x < p.g.vh) {
+    if (x < p.x_end) {
       C v[24];
       C* row = tileH + grp * GS + s * TSTR;
 #pragma unroll
@@ -214,7 +214,7 @@ __device__ __forceinline__ void hop_epilogue(const HopParams& p, typename PT<P>:
       const int j = lowerh ? it2 - nhalf : it2;
       const int g = j / 12, q = j - g * 12;
       const int comp = 8 * (q >> 2) + 4 * lowerh + (q & 3);
-      if (site0 + (nrhs == 1 ? g : g / nrhs) >= p.g.vh) continue;
+      if (site0 + (nrhs == 1 ? g : g / nrhs) >= p.x_end) continue;
       chain_apply_fast(p.fin, comp, tileH + g * GS + comp, TSTR, Ls, mf);
     }
     __syncthreads();
@@ -223,7 +223,7 @@ __device__ __forceinline__ void hop_epilogue(const HopParams& p, typename PT<P>:
       const int r = col / Ls, s = col - r * Ls, grp = site_l * nrhs + r;
       const long long x = site0 + site_l;
       double part = 0.0;
-      if (x < p.g.vh) {
+      if (x < p.x_end) {
         C v[24];
 #pragma unroll
         for (int k = 0; k < 24; k++) v[k] = tileH[grp * GS + s * TSTR + k];

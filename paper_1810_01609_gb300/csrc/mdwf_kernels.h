@@ -29,11 +29,36 @@ struct HopParams {
   float hcf, ccf, mff;   // hc, cc, mf rounded once for the 32-bit kernels
   Red red;
   int* status;        // device flag: nonzero once a bounded device-side wait gave up
+  // sites of the output half this launch covers: x_cb in [x_begin, x_end)
+  long long x_begin, x_end;
+  // T-partitioned lattice: face_mode 1 takes the backward t term (direction 7) of every
+  // site from `face` (the lower neighbour's last timeslice), 2 the forward t term
+  // (direction 3) from the upper neighbour's first timeslice.  A face holds, per face site
+  // f and column, the 12 projected reals the kernel would form (compute type) and, for
+  // F16, the neighbour's norm.  bc_lo / bc_hi: the local first / last timeslice is the
+  // global one (where the time boundary phase applies).
+  int face_mode;
+  const void* face;
+  const float* face_norm;
+  long long face_base;  // checkerboard index of the face's timeslice in the local lattice
+  int bc_lo, bc_hi;
 };
 
 size_t hop_smem_bytes(int prec, const HopParams& p, bool epi);
 // occ: the occupancy-bounded build of a fused 32-bit kernel (ignored otherwise)
 cudaError_t launch_hop(int prec, bool dag, bool r12, bool epi, bool occ, const HopParams& p, cudaStream_t st);
+
+// one face of a T-partitioned lattice (partition.cu): for every site f of the local
+// timeslice starting at checkerboard index `first` (slice_vh sites) and every column, the
+// 12 reals of (1 - sig gamma_4) in projected as the hop kernels project them, in the
+// compute type, at face[(f * W + col) * 12]; F16 also the site's norm at norm[f * W + col]
+struct FaceParams {
+  Field in;
+  long long slice_vh, first;
+  void* face;
+  float* norm;
+};
+cudaError_t launch_pack_face(int prec, int sig, const FaceParams& p, cudaStream_t st);
 
 // tcgen05 tensor-core hop for F16 / BF16 storage (dslash_umma.cu); p.ns = 4D sites per CTA
 bool hop_tc_supported(int prec, const HopParams& p, bool r12);
@@ -58,7 +83,8 @@ struct SLParams {
 cudaError_t launch_chain(int prec, const SLParams& p, cudaStream_t st);
 // a = ca * b + cb * c (b/c may alias a); optional |a|^2 reduction; a.data == nullptr: no store
 cudaError_t launch_axpby(int prec, const SLParams& p, cudaStream_t st);
-// x += alpha p ; p = r + beta p ; phat = chain(p)   (a = p, b = r, c = phat; x separate)
+// x += alpha p ; p = r + beta p ; phat = chain(p)   (a = p, b = r, c = phat; x separate;
+// c.data == nullptr: no phat)
 cudaError_t launch_cg_update(int prec_x, int prec, const SLParams& p, cudaStream_t st);
 // Re <b, c> per rhs into red.out (RED_STORE)
 cudaError_t launch_dot(int prec, const SLParams& p, cudaStream_t st);
@@ -86,6 +112,11 @@ struct GaugeParams {
   int gs;               // stride of the F64 layout (18 or 12)
   double t_bc;
   double* err;          // su3 check max error (device, may be null)
+  // T-partitioned lattice: `user` holds T + 1 timeslices, the first being the lower
+  // neighbour's last one (only its t links are read, for the backward links at t = 0);
+  // bc_lo / bc_hi: the local first / last timeslice is the global one (phase t_bc)
+  int ghost;
+  int bc_lo, bc_hi;
 };
 cudaError_t launch_gauge_load(const GaugeParams& p, cudaStream_t st);
 cudaError_t launch_gauge_convert(int prec, const double* in64, void* out, long long nlinks,

@@ -182,11 +182,13 @@ __global__ void gauge_load_kernel(GaugeParams p) {
   double sign = 1.0;
   if (dir >= 4) {  // U_mu(x - mu)^+
     const int L = mu == 0 ? p.g.X : mu == 1 ? p.g.Y : mu == 2 ? p.g.Z : p.g.T;
-    s[mu] = (s[mu] - 1 + L) % L;
-    if (mu == 3 && c[3] == 0) sign = p.t_bc;
-  } else if (mu == 3 && c[3] == p.g.T - 1) {
+    // with a ghost timeslice t - 1 = -1 is that slice (no wrap)
+    s[mu] = (mu == 3 && p.ghost) ? s[mu] - 1 : (s[mu] - 1 + L) % L;
+    if (mu == 3 && c[3] == 0 && p.bc_lo) sign = p.t_bc;
+  } else if (mu == 3 && c[3] == p.g.T - 1 && p.bc_hi) {
     sign = p.t_bc;
   }
+  if (p.ghost) s[3] += 1;   // user array index: the ghost slice comes first
   const double2* u = (const double2*)p.user + (full_index(p.g, s) * 4 + mu) * 9;
   double2 m[9];
 #pragma unroll

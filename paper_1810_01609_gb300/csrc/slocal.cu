@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(MAXTHREADS) cg_update_kernel(const __grid_cons
     for (int k = 0; k < 24; k++) { pv[k] = rv[k] + bt * pv[k]; tile[(grp * 24 + k) * LsP + s] = pv[k]; }
     store_site<P>(p.a, x_cb, col, pv);
   }
+  if (p.c.data == nullptr) return;   // no phat wanted (the form applies no pre-chain to p)
   __syncthreads();
   const int nitems = p.ns * nrhs * 24;
   for (int it = tid; it < nitems; it += blockDim.x) {

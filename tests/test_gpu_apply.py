@@ -64,6 +64,10 @@ def _oracle(op, Ub, psi, p, par):
         return dirac.mpc_dag(Ub, o(psi), p)
     if op == "MDAGM":
         return dirac.mpc_dag(Ub, dirac.mpc(Ub, o(psi), p), p)
+    if op == "MPC_SYM":
+        return dirac.mpc_sym(Ub, o(psi), p)
+    if op == "MPC_SYM_DAG":
+        return dirac.mpc_sym_dag(Ub, o(psi), p)
     if op == "FULL_D":
         return dirac.mobius(Ub, psi, p)
     if op == "FULL_D_DAG":
@@ -75,7 +79,7 @@ def _mask(op, par, shape):
     """Which parity halves an op writes (the rest of `out` stays zero)."""
     if op in ("HOP_EO", "HOP_EO_DAG", "HOP_EO_M5INV"):
         keep = par == 0
-    elif op in ("HOP_OE", "HOP_OE_DAG", "HOP_OE_M5INV", "MPC", "MPC_DAG", "MDAGM"):
+    elif op in ("HOP_OE", "HOP_OE_DAG", "HOP_OE_M5INV", "MPC", "MPC_DAG", "MDAGM", "MPC_SYM", "MPC_SYM_DAG"):
         keep = par == 1
     else:
         return None
@@ -83,7 +87,8 @@ def _mask(op, par, shape):
 
 
 ALL_OPS = ["HOP_EO", "HOP_OE", "HOP_EO_DAG", "HOP_OE_DAG", "D5", "D5_DAG", "M5", "M5_DAG", "M5INV",
-           "M5INV_DAG", "HOP_EO_M5INV", "HOP_OE_M5INV", "MPC", "MPC_DAG", "MDAGM", "FULL_D", "FULL_D_DAG"]
+           "M5INV_DAG", "HOP_EO_M5INV", "HOP_OE_M5INV", "MPC", "MPC_DAG", "MDAGM", "FULL_D", "FULL_D_DAG",
+           "MPC_SYM", "MPC_SYM_DAG"]
 
 
 @pytest.mark.parametrize("case", CASES)
@@ -126,7 +131,8 @@ def test_tensor_core_hop_matches_oracle(prec, force_ns, monkeypatch):
             continue          # 16 sites of more than 16 columns exceed the tensor-memory budget
         m, ctx, U, Ub, psi, p = _setup(dims, Ls, nrhs)
         par = parity_of(dims)
-        for op in ["HOP_EO", "HOP_OE_DAG", "HOP_OE_M5INV", "MPC", "MPC_DAG", "MDAGM", "FULL_D", "FULL_D_DAG"]:
+        for op in ["HOP_EO", "HOP_OE_DAG", "HOP_OE_M5INV", "MPC", "MPC_DAG", "MDAGM", "FULL_D", "FULL_D_DAG",
+                   "MPC_SYM", "MPC_SYM_DAG"]:
             got = _gpu_apply(m, ctx, op, prec, psi, nrhs)
             ref = np.stack([_oracle(op, Ub, psi[r], p, par) for r in range(nrhs)])
             keep = _mask(op, par, ref.shape)

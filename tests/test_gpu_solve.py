@@ -162,3 +162,21 @@ def test_incremental_residual_tracks_fp64():
     assert len(pairs) >= 2, out.stderr[-2000:]
     for incr, fp64 in pairs:
         assert abs(incr - fp64) <= 1e-2 * fp64, (incr, fp64)
+
+
+@pytest.mark.parametrize("sloppy", ["f64", "f16", "bf16"])
+def test_solve_symmetric_form(sloppy):
+    """pc_form = sym: CG on M_sym y = D5 b~_o, x_o = D5^-1 y.  The full solution is the
+    same unique x = D^-1 b as with the left form (oracle even-odd solve)."""
+    m = lib()
+    dims, Ls, mf = (4, 4, 4, 4), 8, 0.05
+    U, Ub, p, b, xo = _problem(dims, Ls, mf)
+    ctx = m.Context(dims, Ls, mf=mf)
+    ctx.load_gauge(U)
+    x, info = ctx.solve(to_dev(b), tol=1e-10, sloppy=sloppy, pc_form="sym", full_residual=True)
+    x = to_host(x)
+    assert info.status == 0 and info.true_residual <= 1e-10, info.true_residual
+    assert rel(x, xo) <= 1e-8
+    assert solve.residual_full(Ub, b, x, p) <= 1e-9
+    xs, its, res = solve.solve_eo_sym(Ub, b, p, tol=1e-12)
+    assert rel(x, xs) <= 1e-8
