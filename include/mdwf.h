@@ -230,6 +230,15 @@ int mdwf_fh_source(mdwf_ctx* ctx, const double* q4d, double* out4d, int nrhs, in
 int mdwf_contract_nucleon(mdwf_ctx* ctx, const double* u1, const double* d,
                           const double* u2, double* corr, int where, void* stream);
 
+/* Feynman-Hellmann effective coupling (Sec. "Current State of the Art": one sequential
+ * solve with the current at every time gives all source-sink separations): with
+ * R(t) = Re[C_FH(t) / C(t)], geff[t] = R(t+1) - R(t) for t = 0 .. T-2, whose large-t value
+ * is the matrix element (g_A for the gamma_3 gamma_5 current).  c2 = C(t) and c3 = C_FH(t)
+ * are T complex values (2T doubles, HOST), e.g. mdwf_contract_nucleon of S,S,S and the sum
+ * of the contractions with the FH propagator on either u line; geff receives T - 1
+ * doubles (HOST).  MDWF_ERR_ARG if T < 2 or some C(t) is zero or not finite. */
+int mdwf_fh_effective_coupling(const double* c2, const double* c3, double* geff, int T);
+
 /* Allocation-free nucleon contraction (the paper has no counterpart; it serves callers
  * that cannot allocate device memory: code running during CUDA graph capture, programs
  * whose device memory belongs to a pool allocator that forbids other allocations, hosts

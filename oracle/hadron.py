@@ -86,3 +86,14 @@ def nucleon_2pt(U1, D, U2):
     t2 = np.einsum("abcdef,tvafih,tvbeij,tvcdgj->tvgh", ee, u1, dt, u2, optimize=True)
     G = t1 - t2
     return np.einsum("hg,tvgh->t", PROJ_POS, G)
+
+
+def fh_effective_coupling(c2, c3):
+    """Effective coupling from the Feynman-Hellmann correlator (Sec. "Current State of the
+    Art": the FH propagator carries the current at every time, so one extra solve gives
+    all source-sink separations).  With R(t) = Re[C_FH(t) / C(t)], the derivative of
+    log C(t) in the current's coupling, the matrix element is the slope of R at large t:
+        g_eff(t) = R(t+1) - R(t),   t = 0 .. T-2.
+    c2 = C(t), c3 = C_FH(t) (complex, length T)."""
+    r = (np.asarray(c3, dtype=np.complex128) / np.asarray(c2, dtype=np.complex128)).real
+    return r[1:] - r[:-1]

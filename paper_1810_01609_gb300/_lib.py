@@ -82,6 +82,7 @@ _SIGS = {
     "mdwf_contract_nucleon": (_I, [_V, _V, _V, _V, _V, _I, _V]),
     "mdwf_contract_nucleon_noalloc": (_I, [_V, _V, _V, _V, _V, _V]),
     "mdwf_noalloc_last_error": (ctypes.c_char_p, []),
+    "mdwf_fh_effective_coupling": (_I, [_V, _V, _V, _I]),
     "mdwf_set_tuning": (_I, [_V, _I]),
     "mdwf_tune_entries": (_I, [_V, ctypes.POINTER(_I)]),
     "mdwf_tune_entry": (_I, [_V, _I, ctypes.c_char_p, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
@@ -289,3 +290,14 @@ def mdwf_set_face_buffers(ctx, send_lo, send_hi, recv_lo, recv_hi, nbytes):
 def mdwf_group_partitions(ctxs):
     arr = (ctypes.c_void_p * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
     return _check(load().mdwf_group_partitions(arr, len(ctxs)))
+
+
+def mdwf_fh_effective_coupling(c2, c3):
+    """c2 = C(t), c3 = C_FH(t): T complex values (numpy or torch); returns geff (T - 1)."""
+    a = np.ascontiguousarray(np.asarray(c2.cpu() if hasattr(c2, "cpu") else c2, dtype=np.complex128))
+    b = np.ascontiguousarray(np.asarray(c3.cpu() if hasattr(c3, "cpu") else c3, dtype=np.complex128))
+    if a.shape != b.shape or a.ndim != 1:
+        raise ValueError("c2 and c3 must be 1-D of the same length")
+    out = np.empty(a.shape[0] - 1, dtype=np.float64)
+    _check(load().mdwf_fh_effective_coupling(a.ctypes.data, b.ctypes.data, out.ctypes.data, a.shape[0]))
+    return out

@@ -1722,6 +1722,18 @@ int mdwf_contract_nucleon(mdwf_ctx* c, const double* u1, const double* d, const 
   return finish_out(corr, out, (size_t)c->g.T * 16, where, st);
 }
 
+int mdwf_fh_effective_coupling(const double* c2, const double* c3, double* geff, int T) {
+  if (!c2 || !c3 || !geff || T < 2) { g_last_error = "bad argument"; return MDWF_ERR_ARG; }
+  std::vector<double> R(T);
+  for (int t = 0; t < T; t++) {
+    const cd C(c2[2 * t], c2[2 * t + 1]), F(c3[2 * t], c3[2 * t + 1]);
+    if (!(std::abs(C) > 0.0) || !std::isfinite(std::abs(C))) { g_last_error = "C(t) is zero or not finite"; return MDWF_ERR_ARG; }
+    R[t] = (F / C).real();
+  }
+  for (int t = 0; t + 1 < T; t++) geff[t] = R[t + 1] - R[t];
+  return MDWF_SUCCESS;
+}
+
 int mdwf_set_tuning(mdwf_ctx* c, int enable) {
   if (!c) return MDWF_ERR_ARG;
   c->tuning = enable != 0;

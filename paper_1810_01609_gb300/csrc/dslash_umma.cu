@@ -25,8 +25,10 @@
 //
 // Shared-memory operand layout (both operands K-major, no swizzle): a core matrix is 8
 // rows x 16 bytes (8 elements along K) stored as 128 contiguous bytes; the 12 core
-// matrices along K of one 8-row group are 128 bytes apart (leading byte offset) and 8-row
-// groups are 12 x 128 = 1536 bytes apart (stride byte offset).  Site j's A rows are rows
+// matrices along K of one 8-row group are 144 bytes apart (leading byte offset) and 8-row
+// groups 12 x 144 + 16 = 1744 bytes apart (stride byte offset).  The 16-byte gaps skew the
+// shared-memory banks of core matrices, so the 16-byte stores of a warp that all write the
+// same row of different core matrices spread over the banks.  Site j's A rows are rows
 // 24j .. 24j+23 of one shared row sequence: the MMA's M - 24 extra rows read whatever
 // follows (the next sites' rows, other buffers) and produce accumulator rows nobody reads.
 #include "mdwf_impl.cuh"
@@ -40,7 +42,9 @@ namespace {
 constexpr int UM_THREADS = 128;
 constexpr int UM_M = 64;                  // MMA rows: accumulator row 16w + i in TMEM lane 32w + i
 constexpr int UM_KCH = 12;                // K = 96 = 12 core matrices of 8 elements
-constexpr int UM_GRP = UM_KCH * 128;      // bytes per 8-row group
+constexpr int UM_LBO = 144;               // bytes between core matrices along K
+constexpr int UM_GRP = UM_KCH * UM_LBO + 16;   // bytes between 8-row groups
+constexpr int UM_KSTEP = 2 * UM_LBO;      // one MMA's K = 16: two core matrices
 constexpr int UM_WAIT_SPINS = 1 << 24;    // bounded mbarrier waits (about a second)
 
 __host__ __device__ inline int um_npad(int W) { return (W + 15) & ~15; }
@@ -80,7 +84,7 @@ __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvt
 // bits 46-48, no swizzle
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
-  d |= (uint64_t)(128 >> 4) << 16;
+  d |= (uint64_t)(UM_LBO >> 4) << 16;
   d |= (uint64_t)(UM_GRP >> 4) << 32;
   d |= (uint64_t)1 << 46;
   return d;
@@ -109,7 +113,7 @@ __device__ __forceinline__ bool um_wait(uint32_t bar, uint32_t phase) {
         : "=r"(done)
         : "r"(bar), "r"(phase));
     if (done) return true;
-    if (it > 64) __nanosleep(64);
+    if (it >= 8) __nanosleep(128);
   }
   return false;
 }
@@ -180,7 +184,7 @@ __device__ __forceinline__ void link_row(const void* gauge, long long off, int a
   }
 }
 
-// Row o = 8a + 2 sigma + reim of A_x for direction d (K entries 12d..12d+11: slot 0
+// The 8 rows o = 8a + 2 sigma + reim of A_x for direction d (K entries 12d..12d+11: slot 0
 // colours 0..2, slot 1 colours 0..2, each a (re, im) pair), from row a of the link; sg =
 // +-1 is the sign of the direction's projector (1 - sg gamma_mu).  Upper spins sigma = 0, 1
 // take U h of slot sigma; the lower spins take U h of one slot times +-1 or +-i:
@@ -190,39 +194,52 @@ __device__ __forceinline__ void link_row(const void* gauge, long long off, int a
 // A coefficient c times U h in real form: Re(c U h) and Im(c U h) are rows of the pairs
 // P0 = (Re U, -Im U), P1 = (Im U, Re U) and their negatives N0, N1:
 //   c = +1: (P0, P1), -1: (N0, N1), +i: (N1, P0), -i: (P1, N0)   for (re, im) rows.
-__device__ __forceinline__ void write_a_row(unsigned char* A, int j, int d, int o, int sg, const uint32_t row[3]) {
-  const int mu = d & 3, sigma = (o >> 1) & 3, reim = o & 1;
-  int slot, code;                     // code 0: +1, 1: -1, 2: +i, 3: -i
-  if (sigma < 2) {
-    slot = sigma;
-    code = 0;
-  } else {
-    const int t = (sigma - 2) * 4 + mu;
-    slot = (0xC3 >> t) & 1;           // sigma 2: 1 1 0 0, sigma 3: 0 0 1 1
-    code = (int)((0x7662u >> (2 * t)) & 3u);   // sigma 2: 2 0 2 1, sigma 3: 2 1 3 1
-    if (sg < 0) code ^= 1;
-  }
-  // variant: 0 P0, 1 P1, 2 N0, 3 N1 for (code, reim)
-  const int var = (int)((0x93E4u >> (4 * code + 2 * reim)) & 3u);
-  uint32_t v[6];
+template <int MU>
+__device__ __forceinline__ void write_a_rows(unsigned char* A, int j, int d, int a, int sg, const uint32_t row[3]) {
+  uint32_t P0[3], P1[3], N0[3], N1[3];
 #pragma unroll
   for (int b = 0; b < 3; b++) {
-    uint32_t w = (var & 1) ? swp(row[b]) : (row[b] ^ 0x80000000u);
-    if (var & 2) w ^= 0x80008000u;
-    v[b] = slot == 0 ? w : 0u;
-    v[3 + b] = slot == 1 ? w : 0u;
+    P0[b] = row[b] ^ 0x80000000u;
+    P1[b] = swp(row[b]);
+    N0[b] = P0[b] ^ 0x80008000u;
+    N1[b] = P1[b] ^ 0x80008000u;
   }
-  const int grow = 24 * j + o;
-  unsigned char* rowp = A + (grow >> 3) * UM_GRP + (grow & 7) * 16;
-  const int c0 = (12 * d) >> 3;       // core matrix of the direction's first K element
-  if ((d & 1) == 0) {                 // chunk c0 elements 0..7, chunk c0+1 elements 0..3
-    *(uint4*)(rowp + c0 * 128) = make_uint4(v[0], v[1], v[2], v[3]);
-    *(uint2*)(rowp + (c0 + 1) * 128) = make_uint2(v[4], v[5]);
-  } else {                            // chunk c0 elements 4..7, chunk c0+1 elements 0..7
-    *(uint2*)(rowp + c0 * 128 + 8) = make_uint2(v[0], v[1]);
-    *(uint4*)(rowp + (c0 + 1) * 128) = make_uint4(v[2], v[3], v[4], v[5]);
+  constexpr int l0_slot = MU < 2 ? 1 : 0, l1_slot = MU < 2 ? 0 : 1;
+  constexpr int l0_code = MU == 0 ? 2 : MU == 1 ? 0 : MU == 2 ? 2 : 1;   // 0: +1, 1: -1, 2: +i, 3: -i
+  constexpr int l1_code = MU == 0 ? 2 : MU == 1 ? 1 : MU == 2 ? 3 : 1;
+  const int flipc = sg < 0 ? 1 : 0;
+  const int c0 = (12 * d) >> 3;        // core matrix of the direction's first K element
+  unsigned char* grp = A + (3 * j + a) * UM_GRP;
+#pragma unroll
+  for (int sigma = 0; sigma < 4; sigma++) {
+    const int slot = sigma == 0 ? 0 : sigma == 1 ? 1 : sigma == 2 ? l0_slot : l1_slot;
+    const int code = sigma < 2 ? 0 : (sigma == 2 ? l0_code : l1_code) ^ flipc;
+#pragma unroll
+    for (int reim = 0; reim < 2; reim++) {
+      // variant 0 P0, 1 P1, 2 N0, 3 N1 of the (code, reim) row, selected by value
+      const int var = code == 0 ? reim : code == 1 ? 2 + reim : code == 2 ? (reim ? 0 : 3) : (reim ? 2 : 1);
+      uint32_t v[6];
+#pragma unroll
+      for (int b = 0; b < 3; b++) {
+        const uint32_t w = var == 0 ? P0[b] : var == 1 ? P1[b] : var == 2 ? N0[b] : N1[b];
+        v[b] = slot == 0 ? w : 0u;
+        v[3 + b] = slot == 1 ? w : 0u;
+      }
+      unsigned char* rowp = grp + (2 * sigma + reim) * 16;
+      if ((d & 1) == 0) {              // chunk c0 elements 0..7, chunk c0+1 elements 0..3
+        *(uint4*)(rowp + c0 * UM_LBO) = make_uint4(v[0], v[1], v[2], v[3]);
+        *(uint2*)(rowp + (c0 + 1) * UM_LBO) = make_uint2(v[4], v[5]);
+      } else {                         // chunk c0 elements 4..7, chunk c0+1 elements 0..7
+        *(uint2*)(rowp + c0 * UM_LBO + 8) = make_uint2(v[0], v[1]);
+        *(uint4*)(rowp + (c0 + 1) * UM_LBO) = make_uint4(v[2], v[3], v[4], v[5]);
+      }
+    }
   }
 }
+
+// i / w for 0 <= i < 2^16, 1 <= w <= 2^10 without an integer division: the FP32 quotient
+// of i + 1/2 lies at least 1/(2w) from an integer and has a relative error below 2^-23.
+__device__ __forceinline__ int div_small(int i, float inv_w) { return __float2int_rz(((float)i + 0.5f) * inv_w); }
 
 // Projected half spinor of one neighbour chunk set (colours 0..2, 4 spins each):
 // h slot 0 / slot 1 of colour co as (re, im) pairs, (1 - sig gamma_mu) in the chiral basis.
@@ -301,13 +318,13 @@ __device__ __forceinline__ void build_pair(const HopParams& p, const unsigned* n
 #pragma unroll
     for (int i = 0; i < 6; i++) { h0[i] = hmul<P>(h0[i], s0); h1[i] = hmul<P>(h1[i], s1); }
   }
-  *(uint4*)(Bcol + (3 * PQ) * 128) = make_uint4(h0[0], h0[1], h0[2], h0[3]);
-  *(uint4*)(Bcol + (3 * PQ + 1) * 128) = make_uint4(h0[4], h0[5], h1[0], h1[1]);
-  *(uint4*)(Bcol + (3 * PQ + 2) * 128) = make_uint4(h1[2], h1[3], h1[4], h1[5]);
+  *(uint4*)(Bcol + (3 * PQ) * UM_LBO) = make_uint4(h0[0], h0[1], h0[2], h0[3]);
+  *(uint4*)(Bcol + (3 * PQ + 1) * UM_LBO) = make_uint4(h0[4], h0[5], h1[0], h1[1]);
+  *(uint4*)(Bcol + (3 * PQ + 2) * UM_LBO) = make_uint4(h1[2], h1[3], h1[4], h1[5]);
 }
 
 template <int P, bool DAG, bool R12, bool EPI>
-__global__ void __launch_bounds__(UM_THREADS) hop_umma_kernel(const __grid_constant__ HopParams p) {
+__global__ void __launch_bounds__(UM_THREADS, 4) hop_umma_kernel(const __grid_constant__ HopParams p) {
   using C = float;
   extern __shared__ __align__(1024) unsigned char smem[];
   const int Ls = p.in.Ls, nrhs = p.in.nrhs, W = Ls * nrhs;
@@ -346,18 +363,24 @@ __global__ void __launch_bounds__(UM_THREADS) hop_umma_kernel(const __grid_const
   }
   __syncthreads();
 
-  // link matrices, one thread per (site, direction, output row): consecutive threads
-  // write consecutive rows, i.e. distinct 16-byte bank groups of a core matrix
-  for (int i = tid; i < nact * 192; i += UM_THREADS) {
-    const int j = i / 192, rem = i - j * 192, d = rem / 24, o = rem - d * 24;
+  // link matrices, one thread per (site, direction, colour row a): 8 rows of 12 entries
+  for (int i = tid; i < nact * 24; i += UM_THREADS) {
+    const int j = i / 24, r = i - j * 24, d = r / 3, a = r - d * 3;
     uint32_t row[3];
-    link_row<P, R12>(p.gauge, ((site0 + j) * 8 + d) * p.gs, o >> 3, sflip[j * 8 + d] != 0, row);
-    write_a_row(A, j, d, o, d < 4 ? SF : -SF, row);
+    link_row<P, R12>(p.gauge, ((site0 + j) * 8 + d) * p.gs, a, sflip[j * 8 + d] != 0, row);
+    const int sg = d < 4 ? SF : -SF;
+    switch (d & 3) {
+      case 0: write_a_rows<0>(A, j, d, a, sg, row); break;
+      case 1: write_a_rows<1>(A, j, d, a, sg, row); break;
+      case 2: write_a_rows<2>(A, j, d, a, sg, row); break;
+      default: write_a_rows<3>(A, j, d, a, sg, row); break;
+    }
   }
 
   // phase 1: projected neighbours (B operand), one thread per (site, direction pair, column)
+  const float inv_w = 1.0f / (float)W;
   for (int i = tid; i < nact * 4 * W; i += UM_THREADS) {
-    const int j = i / (4 * W), rem = i - j * 4 * W, pq = rem / W, n = rem - pq * W;
+    const int jq = div_small(i, inv_w), n = i - jq * W, j = jq >> 2, pq = jq & 3;
     const unsigned* nb = snbr + j * 8;
     float inv = 1.0f;
     if constexpr (P == F16) {
@@ -384,52 +407,59 @@ __global__ void __launch_bounds__(UM_THREADS) hop_umma_kernel(const __grid_const
   const uint32_t tbase = *tslot;
   const uint32_t bar_a = su32(bar);
 
-  // phase 2: the contraction, 6 MMAs (K = 16 each) per site, issued by one thread
+  // phase 2: the contraction, 6 MMAs (K = 16 each) per site, issued by one thread, which
+  // also waits for their completion (the other threads wait at the barrier)
+  int* okflag = (int*)(smem + L.bar + 12);
   if (tid == 0) {
     const uint32_t idesc = um_idesc<P>(L.npad);
     const uint32_t a0 = su32(A), b0 = su32(B);
     for (int j = 0; j < nact; j++) {
 #pragma unroll
       for (int ks = 0; ks < 6; ks++)
-        um_mma(tbase + (uint32_t)(j * L.npad), sdesc(a0 + 3 * j * UM_GRP + ks * 256),
-               sdesc(b0 + j * (L.npad / 8) * UM_GRP + ks * 256), idesc, ks > 0 ? 1u : 0u);
+        um_mma(tbase + (uint32_t)(j * L.npad), sdesc(a0 + 3 * j * UM_GRP + ks * UM_KSTEP),
+               sdesc(b0 + j * (L.npad / 8) * UM_GRP + ks * UM_KSTEP), idesc, ks > 0 ? 1u : 0u);
     }
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar_a)
                  : "memory");
+    bool ok = um_wait(bar_a, 0);
+    if (!ok) {
+      if (p.status) atomicOr(p.status, 1);
+      ok = um_wait(bar_a, 0);   // a second bounded wait before the accumulators are read or released
+    }
+    *okflag = ok ? 1 : 0;
+    fence_before();
   }
+  __syncthreads();
+  fence_after();
 
   // phase 3: accumulators -> epilogue tile.  With M = 64 accumulator row 16w + i sits in
   // TMEM lane 32w + i (i < 16), which only warp w may read: rows 0..15 go through warp 0,
   // rows 16..23 through warp 1.
   C* tileH = (C*)(smem + L.tile);
   const int GS = tile_gstr(Ls);
-  if (warp < 2) {
-    const bool ok = um_wait(bar_a, 0);
-    fence_after();
+  if (warp < 2 && *okflag) {
     const int o = 16 * warp + lane;                  // accumulator row of this lane
     const bool mine = lane < (warp == 0 ? 16 : 8);
-    if (ok) {
-      for (int j = 0; j < nact; j++) {
-        for (int c0 = 0; c0 < W; c0 += 16) {
-          float v[16];
-          um_ld16(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(j * L.npad + c0), v);
-          if (mine) {
+    const float inv_ls = 1.0f / (float)Ls;
+    for (int j = 0; j < nact; j++) {
+      for (int c0 = 0; c0 < W; c0 += 16) {
+        float v[16];
+        um_ld16(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(j * L.npad + c0), v);
+        if (mine) {
+          int r = div_small(c0, inv_ls), s = c0 - r * Ls;   // column n = r Ls + s, walked in order
+          C* dst = tileH + (j * nrhs + r) * GS + s * TSTR + o;
 #pragma unroll
-            for (int q = 0; q < 16; q++) {
-              const int n = c0 + q;
-              if (n < W) {
-                const int r = n / Ls, s = n - r * Ls;
-                float sc = 1.0f;
-                if constexpr (P == F16) sc = nmax[j * L.npad + n];
-                tileH[(j * nrhs + r) * GS + s * TSTR + o] = v[q] * sc;
-              }
+          for (int q = 0; q < 16; q++) {
+            if (c0 + q < W) {
+              float sc = 1.0f;
+              if constexpr (P == F16) sc = nmax[j * L.npad + c0 + q];
+              *dst = v[q] * sc;
             }
+            dst += TSTR;
+            if (++s == Ls) { s = 0; dst += GS - Ls * TSTR; }
           }
         }
       }
-    } else {
-      if (lane == 0 && p.status) atomicOr(p.status, 1);
-      um_wait(bar_a, 0);   // a second bounded wait before the accumulators are released
     }
   }
   fence_before();

@@ -88,6 +88,12 @@ def test_point_propagator_fh_chain():
     CFo = hadron.nucleon_2pt(_cols_to_oracle(SFo), _cols_to_oracle(So), _cols_to_oracle(So)) + \
         hadron.nucleon_2pt(_cols_to_oracle(So), _cols_to_oracle(So), _cols_to_oracle(SFo))
     assert rel(CF, CFo) <= 1e-8
+    # the effective-coupling estimator of the product against the oracle's on the oracle's
+    # correlators (bit-level), and on the GPU correlators within their parity bound
+    assert np.max(np.abs(m.mdwf_fh_effective_coupling(Co, CFo) - hadron.fh_effective_coupling(Co, CFo))) <= \
+        1e-13 * np.max(np.abs(hadron.fh_effective_coupling(Co, CFo)))
+    g, go = m.mdwf_fh_effective_coupling(C, CF), hadron.fh_effective_coupling(Co, CFo)
+    assert np.max(np.abs(g - go)) <= 1e-6 * max(1.0, np.max(np.abs(go)))
 
 
 def test_gauge_errors():

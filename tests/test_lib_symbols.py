@@ -81,3 +81,23 @@ def test_struct_layouts_match_header(tmp_path):
         assert int(got[sname]) == ctypes.sizeof(cls), sname
         for fname, _ in cls._fields_:
             assert int(got["%s.%s" % (sname, fname)]) == getattr(cls, fname).offset, (sname, fname)
+
+
+def test_fh_effective_coupling_matches_oracle():
+    """Host-side C function of the library against the oracle's estimator (no GPU)."""
+    import __graft_entry__
+    __graft_entry__.build()
+    import numpy as np
+    import paper_1810_01609_gb300 as m
+    from oracle import hadron
+    rng = np.random.default_rng(3)
+    c2 = rng.standard_normal(12) + 1j * rng.standard_normal(12)
+    c3 = rng.standard_normal(12) + 1j * rng.standard_normal(12)
+    got = m.mdwf_fh_effective_coupling(c2, c3)
+    assert np.max(np.abs(got - hadron.fh_effective_coupling(c2, c3))) <= 1e-13 * np.max(np.abs(got))
+    c2[5] = 0.0
+    try:
+        m.mdwf_fh_effective_coupling(c2, c3)
+        raise AssertionError("accepted C(t) = 0")
+    except m.MdwfError as e:
+        assert e.code == m.MDWF_ERR_ARG

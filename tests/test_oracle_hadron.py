@@ -123,3 +123,21 @@ def test_nucleon_gauge_invariance():
     # the propagator transforms as Om(x) S(x) Om(0)^+
     rotS = np.einsum("tzyxab,tzyxibjc->tzyxiajc", Om, S)
     assert np.abs(Sg - rotS).max() < 1e-9 * np.abs(S).max()
+
+
+def test_fh_effective_coupling_closed_form():
+    """C(t) = A e^{-Mt}(1 + a e^{-Dt}) e^{i phi}, C_FH(t) = C(t) (c0 + g t): the ratio is
+    linear in t, so g_eff(t) = g at every t, whatever the phase and excited state."""
+    from oracle import hadron
+    T = 16
+    t = np.arange(T)
+    C = 0.7 * np.exp(-0.45 * t) * (1 + 0.3 * np.exp(-0.6 * t)) * np.exp(0.37j)
+    CF = C * (1.9 + 1.27 * t)
+    g = hadron.fh_effective_coupling(C, CF)
+    assert g.shape == (T - 1,)
+    assert np.max(np.abs(g - 1.27)) < 1e-12
+    # an excited-state term in the FH correlator decays out of the slope
+    CF2 = C * (1.9 + 1.27 * t + 0.5 * np.exp(-1.1 * t))
+    g2 = hadron.fh_effective_coupling(C, CF2)
+    d = 0.5 * (np.exp(-1.1 * (t[:-1] + 1)) - np.exp(-1.1 * t[:-1]))
+    assert np.max(np.abs(g2 - (1.27 + d))) < 1e-12
