@@ -282,20 +282,22 @@ def kernel_only(args, m, ctx, dims, Ls, seed, stream):
     import torch
     import inputs
     prec = m.PRECS[args.sloppy]
-    nb = ctx.field_bytes(args.sloppy, 1)
+    nr = args.nrhs
+    nb = ctx.field_bytes(args.sloppy, nr)
     fin = torch.zeros(nb, dtype=torch.uint8, device="cuda")
     fout = torch.zeros(nb, dtype=torch.uint8, device="cuda")
-    src = torch.from_numpy(inputs.gaussian_spinor5d(dims, Ls, seed + 100)).cuda()
-    m.mdwf_pack(ctx.h, src, fin, prec, 1, stream)
-    m.mdwf_apply(ctx.h, m.OP[args.op], prec, fin, fout, 1, stream)
+    src = inputs.gaussian_spinor5d_device(dims, Ls, seed + 100, nrhs=nr)
+    m.mdwf_pack(ctx.h, src, fin, prec, nr, stream)
+    del src
+    m.mdwf_apply(ctx.h, m.OP[args.op], prec, fin, fout, nr, stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.kernel_launches):
-        m.mdwf_apply(ctx.h, m.OP[args.op], prec, fin, fout, 1, stream)
+        m.mdwf_apply(ctx.h, m.OP[args.op], prec, fin, fout, nr, stream)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / max(1, args.kernel_launches)
-    print(json.dumps({"kernel_only": args.op, "launches": args.kernel_launches, "ms_per_launch": ms,
+    print(json.dumps({"kernel_only": args.op, "nrhs": nr, "launches": args.kernel_launches, "ms_per_launch": ms,
                       "tune": ctx.tune_entries()}))
 
 
@@ -474,6 +476,7 @@ def main():
     ap.add_argument("--kernel-only", action="store_true",
                     help="only launch the fused hop + M5^-1 kernel a few times (for ncu captures)")
     ap.add_argument("--op", default="HOP_OE_M5INV")
+    ap.add_argument("--nrhs", type=int, default=1, help="kernel-only: right-hand sides per launch")
     ap.add_argument("--print-hash", action="store_true", help="print the kernel-source hash and exit")
     args = ap.parse_args()
     wl = args.workload

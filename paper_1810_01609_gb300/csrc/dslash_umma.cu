@@ -194,8 +194,8 @@ __device__ __forceinline__ void link_row(const void* gauge, long long off, int a
 // A coefficient c times U h in real form: Re(c U h) and Im(c U h) are rows of the pairs
 // P0 = (Re U, -Im U), P1 = (Im U, Re U) and their negatives N0, N1:
 //   c = +1: (P0, P1), -1: (N0, N1), +i: (N1, P0), -i: (P1, N0)   for (re, im) rows.
-template <int MU>
-__device__ __forceinline__ void write_a_rows(unsigned char* A, int j, int d, int a, int sg, const uint32_t row[3]) {
+template <int MU, int SG>
+__device__ __forceinline__ void write_a_rows(unsigned char* A, int j, int d, int a, const uint32_t row[3]) {
   uint32_t P0[3], P1[3], N0[3], N1[3];
 #pragma unroll
   for (int b = 0; b < 3; b++) {
@@ -207,13 +207,13 @@ __device__ __forceinline__ void write_a_rows(unsigned char* A, int j, int d, int
   constexpr int l0_slot = MU < 2 ? 1 : 0, l1_slot = MU < 2 ? 0 : 1;
   constexpr int l0_code = MU == 0 ? 2 : MU == 1 ? 0 : MU == 2 ? 2 : 1;   // 0: +1, 1: -1, 2: +i, 3: -i
   constexpr int l1_code = MU == 0 ? 2 : MU == 1 ? 1 : MU == 2 ? 3 : 1;
-  const int flipc = sg < 0 ? 1 : 0;
+  constexpr int flipc = SG < 0 ? 1 : 0;
   const int c0 = (12 * d) >> 3;        // core matrix of the direction's first K element
   unsigned char* grp = A + (3 * j + a) * UM_GRP;
 #pragma unroll
   for (int sigma = 0; sigma < 4; sigma++) {
     const int slot = sigma == 0 ? 0 : sigma == 1 ? 1 : sigma == 2 ? l0_slot : l1_slot;
-    const int code = sigma < 2 ? 0 : (sigma == 2 ? l0_code : l1_code) ^ flipc;
+    const int code = sigma < 2 ? 0 : (sigma == 2 ? l0_code : l1_code) ^ flipc;   // compile-time
 #pragma unroll
     for (int reim = 0; reim < 2; reim++) {
       // variant 0 P0, 1 P1, 2 N0, 3 N1 of the (code, reim) row, selected by value
@@ -368,12 +368,15 @@ __global__ void __launch_bounds__(UM_THREADS, 4) hop_umma_kernel(const __grid_co
     const int j = i / 24, r = i - j * 24, d = r / 3, a = r - d * 3;
     uint32_t row[3];
     link_row<P, R12>(p.gauge, ((site0 + j) * 8 + d) * p.gs, a, sflip[j * 8 + d] != 0, row);
-    const int sg = d < 4 ? SF : -SF;
-    switch (d & 3) {
-      case 0: write_a_rows<0>(A, j, d, a, sg, row); break;
-      case 1: write_a_rows<1>(A, j, d, a, sg, row); break;
-      case 2: write_a_rows<2>(A, j, d, a, sg, row); break;
-      default: write_a_rows<3>(A, j, d, a, sg, row); break;
+    switch (d) {   // forward directions project with SF, backward ones with -SF
+      case 0: write_a_rows<0, SF>(A, j, d, a, row); break;
+      case 1: write_a_rows<1, SF>(A, j, d, a, row); break;
+      case 2: write_a_rows<2, SF>(A, j, d, a, row); break;
+      case 3: write_a_rows<3, SF>(A, j, d, a, row); break;
+      case 4: write_a_rows<0, -SF>(A, j, d, a, row); break;
+      case 5: write_a_rows<1, -SF>(A, j, d, a, row); break;
+      case 6: write_a_rows<2, -SF>(A, j, d, a, row); break;
+      default: write_a_rows<3, -SF>(A, j, d, a, row); break;
     }
   }
 
@@ -441,6 +444,19 @@ __global__ void __launch_bounds__(UM_THREADS, 4) hop_umma_kernel(const __grid_co
     const int o = 16 * warp + lane;                  // accumulator row of this lane
     const bool mine = lane < (warp == 0 ? 16 : 8);
     const float inv_ls = 1.0f / (float)Ls;
+    if (W <= 16) {   // one right-hand side of Ls <= 16: column n is slice s, one load per site
+      for (int j = 0; j < nact; j++) {
+        float v[16];
+        um_ld16(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(j * L.npad), v);
+        if (mine) {
+          C* dst = tileH + j * nrhs * GS + o;
+          const float* sc = nmax + j * L.npad;
+#pragma unroll
+          for (int q = 0; q < 16; q++)
+            if (q < W) dst[q * TSTR] = P == F16 ? v[q] * sc[q] : v[q];
+        }
+      }
+    } else
     for (int j = 0; j < nact; j++) {
       for (int c0 = 0; c0 < W; c0 += 16) {
         float v[16];
