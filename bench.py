@@ -468,7 +468,7 @@ def main():
     ap.add_argument("--workload", default="24^3x64_Ls10", choices=sorted(WORKLOADS) + list(MODES))
     ap.add_argument("--group", type=int, default=3, help="batch32: right-hand sides per multi-RHS launch")
     ap.add_argument("--fp64-solves", type=int, default=16, help="graphbatch: solves repeated with plain FP64")
-    ap.add_argument("--sloppy", default="f16", choices=["f16", "bf16", "f32"])
+    ap.add_argument("--sloppy", default="f16", choices=["f16", "bf16", "f32", "i16"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--kernel-launches", type=int, default=20)
@@ -589,8 +589,8 @@ def main():
         kt.append(a.elapsed_time(b))
     kms = float(np.mean(kt))
     vh = V // 2
-    site = {"f16": 52.0, "bf16": 48.0, "f32": 96.0}[args.sloppy]
-    link = {"f16": 2, "bf16": 2, "f32": 4}[args.sloppy] * 18.0
+    site = {"f16": 52.0, "bf16": 48.0, "f32": 96.0, "i16": 52.0}[args.sloppy]
+    link = {"f16": 2, "bf16": 2, "f32": 4, "i16": 2}[args.sloppy] * 18.0
     kbytes = vh * Ls * 2 * site + vh * 8 * link
     peak, peak_kind = peaks()
     achieved = kbytes / (kms * 1e-3) / 1e9

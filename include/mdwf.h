@@ -67,7 +67,11 @@ enum mdwf_precision {
   MDWF_PREC_F64 = 0,   /* double storage, double arithmetic */
   MDWF_PREC_F32 = 1,   /* float storage, float arithmetic */
   MDWF_PREC_F16 = 2,   /* half storage + one float norm per 5D site, float arithmetic */
-  MDWF_PREC_BF16 = 3   /* bfloat16 storage, float arithmetic */
+  MDWF_PREC_BF16 = 3,  /* bfloat16 storage, float arithmetic */
+  MDWF_PREC_I16 = 4    /* 16-bit fixed point (the paper's "16-bit fixed-point storage"): per
+                          5D site one float norm = max |component| and 24 int16
+                          q = RNE(32767 v / norm); links q = RNE(32767 u); float arithmetic
+                          (CUDA-core hop only) */
 };
 
 enum mdwf_location { MDWF_HOST = 0, MDWF_DEVICE = 1 };
@@ -181,8 +185,9 @@ int mdwf_load_gauge(mdwf_ctx* ctx, const double* links, int where, void* stream)
 int mdwf_field_bytes(const mdwf_ctx* ctx, int prec, int nrhs, size_t* bytes);
 
 /* user5d (DEVICE, complex128 [nrhs][s][t][z][y][x][4][3]) -> internal field (DEVICE).
- * F16 stores per 5D site norm = float(max |component|) and halves = RNE(v / norm);
- * BF16 and F32 are RNE conversions. */
+ * F16 stores per 5D site norm = float(max |component|) and halves = RNE(v / norm); I16
+ * the same norm and int16 RNE(32767 v / norm) (FP64 product, then quotient); BF16 and
+ * F32 are RNE conversions. */
 int mdwf_pack(mdwf_ctx* ctx, const double* user5d, void* internal, int prec, int nrhs,
               void* stream);
 /* internal field (DEVICE) -> user5d (DEVICE, complex128). */

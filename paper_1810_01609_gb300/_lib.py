@@ -22,8 +22,8 @@ MDWF_ERR_BREAKDOWN = -6
 MDWF_ERR_TIMEOUT = -7
 MDWF_ERR_STATE = -8
 
-MDWF_PREC_F64, MDWF_PREC_F32, MDWF_PREC_F16, MDWF_PREC_BF16 = 0, 1, 2, 3
-PRECS = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+MDWF_PREC_F64, MDWF_PREC_F32, MDWF_PREC_F16, MDWF_PREC_BF16, MDWF_PREC_I16 = 0, 1, 2, 3, 4
+PRECS = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "i16": 4}
 MDWF_HOST, MDWF_DEVICE = 0, 1
 MDWF_PC_LEFT, MDWF_PC_SYM = 0, 1
 PC_FORMS = {"left": 0, "sym": 1}

@@ -197,7 +197,7 @@ int ws_half(mdwf_ctx* c, const std::string& name, int prec, int nrhs, Field* f) 
   return MDWF_SUCCESS;
 }
 // algorithmic bytes of one 5D site of a field in storage precision prec
-double site_bytes(int prec) { return prec == F64 ? 192.0 : prec == F32 ? 96.0 : prec == F16 ? 52.0 : 48.0; }
+double site_bytes(int prec) { return prec == F64 ? 192.0 : prec == F32 ? 96.0 : (prec == F16 || prec == I16) ? 52.0 : 48.0; }
 double half_bytes(const Field& f, int prec) { return (double)f.vh * f.nrhs * f.Ls * site_bytes(prec); }
 // links: 18 (or 12) reals per link, 8 links per output 4D site
 double gauge_bytes(const mdwf_ctx* c, int prec) {
@@ -1307,6 +1307,9 @@ int mdwf_create(const mdwf_params* p, mdwf_ctx** out) {
   for (int i = 0; i < 4; i++)
     if (p->dims[i] < 2 || (p->dims[i] & 1)) { g_last_error = "dims must be even and >= 2"; return MDWF_ERR_ARG; }
   if (p->Ls < 2 || p->Ls > MAXLS) { g_last_error = "Ls out of range [2, 32]"; return MDWF_ERR_ARG; }
+  if ((double)p->dims[0] * p->dims[1] * p->dims[2] * p->dims[3] >= 4294967296.0) {
+    g_last_error = "lattice too large (more than 2^32 sites)"; return MDWF_ERR_ARG;
+  }
   if (p->gauge_recon != 18 && p->gauge_recon != 12) { g_last_error = "gauge_recon must be 18 or 12"; return MDWF_ERR_ARG; }
   if (p->gauge_recon == 12 && std::fabs(p->t_bc) != 1.0) { g_last_error = "recon 12 needs t_bc = +-1"; return MDWF_ERR_ARG; }
   if (p->t_ranks < 1 || p->t_rank < 0 || p->t_rank >= p->t_ranks) { g_last_error = "bad t_ranks / t_rank"; return MDWF_ERR_ARG; }
@@ -1327,6 +1330,9 @@ int mdwf_create(const mdwf_params* p, mdwf_ctx** out) {
   c->device = dev;
   c->g.X = p->dims[0]; c->g.Y = p->dims[1]; c->g.Z = p->dims[2]; c->g.T = p->dims[3];
   c->g.Xh = p->dims[0] / 2;
+  c->g.fXh = make_fastdiv((uint32_t)c->g.Xh);
+  c->g.fY = make_fastdiv((uint32_t)p->dims[1]);
+  c->g.fZ = make_fastdiv((uint32_t)p->dims[2]);
   c->vh = (long long)p->dims[0] * p->dims[1] * p->dims[2] * p->dims[3] / 2;
   c->g.vh = c->vh;
   c->slice_vh = (long long)p->dims[0] * p->dims[1] * p->dims[2] / 2;
@@ -1421,7 +1427,7 @@ int mdwf_load_gauge(mdwf_ctx* c, const double* links, int where, void* stream) {
 }
 
 int mdwf_field_bytes(const mdwf_ctx* c, int prec, int nrhs, size_t* bytes) {
-  if (!c || !bytes || prec < 0 || prec > 3 || nrhs < 1) { g_last_error = "bad argument"; return MDWF_ERR_ARG; }
+  if (!c || !bytes || prec < 0 || prec > 4 || nrhs < 1) { g_last_error = "bad argument"; return MDWF_ERR_ARG; }
   *bytes = full_bytes(c, prec, nrhs);
   return MDWF_SUCCESS;
 }
@@ -1432,7 +1438,7 @@ static int check_nrhs(const mdwf_ctx* c, int nrhs) {
 }
 
 int mdwf_pack(mdwf_ctx* c, const double* user5d, void* internal, int prec, int nrhs, void* stream) {
-  if (!c || !user5d || !internal || prec < 0 || prec > 3 || nrhs < 1) { g_last_error = "bad argument"; return MDWF_ERR_ARG; }
+  if (!c || !user5d || !internal || prec < 0 || prec > 4 || nrhs < 1) { g_last_error = "bad argument"; return MDWF_ERR_ARG; }
   PackParams p;
   p.g = c->g; p.Ls = c->Ls; p.nrhs = nrhs; p.user = user5d; p.user_out = nullptr;
   for (int q = 0; q < 2; q++) {
@@ -1446,7 +1452,7 @@ int mdwf_pack(mdwf_ctx* c, const double* user5d, void* internal, int prec, int n
 }
 
 int mdwf_unpack(mdwf_ctx* c, const void* internal, double* user5d, int prec, int nrhs, void* stream) {
-  if (!c || !user5d || !internal || prec < 0 || prec > 3 || nrhs < 1) { g_last_error = "bad argument"; return MDWF_ERR_ARG; }
+  if (!c || !user5d || !internal || prec < 0 || prec > 4 || nrhs < 1) { g_last_error = "bad argument"; return MDWF_ERR_ARG; }
   PackParams p;
   p.g = c->g; p.Ls = c->Ls; p.nrhs = nrhs; p.user = nullptr; p.user_out = user5d;
   for (int q = 0; q < 2; q++) {
@@ -1460,7 +1466,7 @@ int mdwf_unpack(mdwf_ctx* c, const void* internal, double* user5d, int prec, int
 }
 
 int mdwf_apply(mdwf_ctx* c, int op, int prec, const void* in, void* out, int nrhs, void* stream) {
-  if (!c || !in || !out || prec < 0 || prec > 3 || op < 0 || op >= MDWF_OP_COUNT || in == out) {
+  if (!c || !in || !out || prec < 0 || prec > 4 || op < 0 || op >= MDWF_OP_COUNT || in == out) {
     g_last_error = "bad argument"; return MDWF_ERR_ARG;
   }
   CKS(check_nrhs(c, nrhs));
@@ -1513,7 +1519,7 @@ int mdwf_solve_multi(mdwf_ctx* c, int nrhs, const double* src, double* sol, cons
   const auto t0 = std::chrono::steady_clock::now();
   if (!c || !src || !sol || !sp || !info) { g_last_error = "null pointer"; return MDWF_ERR_ARG; }
   CKS(check_nrhs(c, nrhs));
-  if (sp->sloppy_prec < 0 || sp->sloppy_prec > 3 || !(sp->tol > 0.0) || sp->maxiter < 1 ||
+  if (sp->sloppy_prec < 0 || sp->sloppy_prec > 4 || !(sp->tol > 0.0) || sp->maxiter < 1 ||
       (sp->location != MDWF_HOST && sp->location != MDWF_DEVICE) || !(sp->delta > 0.0 && sp->delta < 1.0) ||
       sp->ru_interval < 1 || (sp->pc_form != MDWF_PC_LEFT && sp->pc_form != MDWF_PC_SYM)) {
     g_last_error = "bad solve parameters"; return MDWF_ERR_ARG;
@@ -1769,7 +1775,7 @@ int mdwf_set_face_exchange(mdwf_ctx* c, mdwf_face_exchange_fn fn, void* user) {
 }
 
 int mdwf_face_bytes(const mdwf_ctx* c, int prec, int nrhs, size_t* bytes) {
-  if (!c || !bytes || prec < 0 || prec > 3 || nrhs < 1) { g_last_error = "bad argument"; return MDWF_ERR_ARG; }
+  if (!c || !bytes || prec < 0 || prec > 4 || nrhs < 1) { g_last_error = "bad argument"; return MDWF_ERR_ARG; }
   *bytes = face_bytes_of(c, prec, nrhs);
   return MDWF_SUCCESS;
 }

@@ -29,6 +29,7 @@ cudaError_t launch_hop(int prec, bool dag, bool r12, bool epi, bool occ, const H
     case F32: return launch_hop_prec<F32>(p, dag, r12, epi, occ, threads, smem, st);
     case F16: return launch_hop_prec<F16>(p, dag, r12, epi, occ, threads, smem, st);
     case BF16: return launch_hop_prec<BF16>(p, dag, r12, epi, occ, threads, smem, st);
+    case I16: return launch_hop_prec<I16>(p, dag, r12, epi, occ, threads, smem, st);
   }
   return cudaErrorInvalidValue;
 }

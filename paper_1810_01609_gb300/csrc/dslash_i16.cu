@@ -1,0 +1,7 @@
+// 16-bit fixed-point (int16 + norm) instantiations of the CUDA-core hop kernels (see
+// dslash_impl.cuh).
+#include "dslash_impl.cuh"
+
+namespace mdwf {
+template cudaError_t launch_hop_prec<I16>(const HopParams&, bool, bool, bool, bool, int, size_t, cudaStream_t);
+}  // namespace mdwf

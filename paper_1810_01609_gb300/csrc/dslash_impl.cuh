@@ -108,6 +108,7 @@ __device__ __forceinline__ void load_link(const void* base, long long off, typen
     for (int i = 0; i < NR / 2; i++) {
       float2 f;
       if constexpr (P == F16) f = __half22float2(*(const __half2*)&t[i]);
+      else if constexpr (P == I16) { f = i16x2_to_float2(t[i]); f.x *= I16_INV; f.y *= I16_INV; }
       else f = __bfloat1622float2(*(const __nv_bfloat162*)&t[i]);
       U[2 * i] = f.x; U[2 * i + 1] = f.y;
     }
@@ -178,9 +179,28 @@ __device__ __forceinline__ auto mk2(float a, float b) {
 template <int P, int MU, int SIG>
 __device__ __forceinline__ typename PT<P>::C load_proj(const Field& f, unsigned nbr, int col, typename PT<P>::C h[12]) {
   using C = typename PT<P>::C;
-  if constexpr (P == F64 || P == F32) {
+  if constexpr (P == F64 || P == F32 || P == I16) {
     C psi[24];
-    load_site<P>(f, nbr, col, psi);
+    C nrm = (C)1;
+    if constexpr (P == I16) {
+      // exact integers projected in FP32; the site's scale norm / 32767 is returned and
+      // folded into the accumulation like the F16 norm
+      const uint4* d = (const uint4*)f.data;
+      const unsigned W = (unsigned)f.W();
+      nrm = __ldg(f.norm + nbr * W + col) * I16_INV;
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        const uint4 q = __ldg(d + (nbr * 3 + c) * W + col);
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          const float2 fv = i16x2_to_float2(w[j]);
+          psi[8 * c + 2 * j] = fv.x; psi[8 * c + 2 * j + 1] = fv.y;
+        }
+      }
+    } else {
+      load_site<P>(f, nbr, col, psi);
+    }
     const C sg = (C)SIG;
 #pragma unroll
     for (int co = 0; co < 3; co++) {
@@ -200,7 +220,7 @@ __device__ __forceinline__ typename PT<P>::C load_proj(const Field& f, unsigned 
         h1[0] = PRE(1, co) - sg * PRE(3, co); h1[1] = PIM(1, co) - sg * PIM(3, co);
       }
     }
-    return (C)1;
+    return nrm;
   } else {
     using H2 = typename std::conditional<P == F16, __half2, __nv_bfloat162>::type;
     const uint4* d = (const uint4*)f.data;

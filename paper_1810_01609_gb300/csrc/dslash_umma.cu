@@ -237,10 +237,6 @@ __device__ __forceinline__ void write_a_rows(unsigned char* A, int j, int d, int
   }
 }
 
-// i / w for 0 <= i < 2^16, 1 <= w <= 2^10 without an integer division: the FP32 quotient
-// of i + 1/2 lies at least 1/(2w) from an integer and has a relative error below 2^-23.
-__device__ __forceinline__ int div_small(int i, float inv_w) { return __float2int_rz(((float)i + 0.5f) * inv_w); }
-
 // Projected half spinor of one neighbour chunk set (colours 0..2, 4 spins each):
 // h slot 0 / slot 1 of colour co as (re, im) pairs, (1 - sig gamma_mu) in the chiral basis.
 template <int P, int MU, int SIG>
@@ -444,7 +440,7 @@ __global__ void __launch_bounds__(UM_THREADS, 4) hop_umma_kernel(const __grid_co
     const int o = 16 * warp + lane;                  // accumulator row of this lane
     const bool mine = lane < (warp == 0 ? 16 : 8);
     const float inv_ls = 1.0f / (float)Ls;
-    if (W <= 16) {   // one right-hand side of Ls <= 16: column n is slice s, one load per site
+    if (nrhs == 1 && W <= 16) {   // one right-hand side of Ls <= 16: column n is slice s, one load per site
       for (int j = 0; j < nact; j++) {
         float v[16];
         um_ld16(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(j * L.npad), v);

@@ -34,6 +34,7 @@ __device__ __forceinline__ void load_chunk(const Field& f, long long x_cb, int c
     for (int j = 0; j < 4; j++) {
       float2 v;
       if constexpr (P == F16) v = __half22float2(*(const __half2*)&w[j]);
+      else if constexpr (P == I16) v = i16x2_to_float2(w[j]);
       else v = __bfloat1622float2(*(const __nv_bfloat162*)&w[j]);
       out[2 * j] = v.x * nrm; out[2 * j + 1] = v.y * nrm;
     }
@@ -61,6 +62,7 @@ template <int P>
 __device__ __forceinline__ float2 pair16(const uint4& q, int j) {
   const uint32_t w = j == 0 ? q.x : j == 1 ? q.y : j == 2 ? q.z : q.w;
   if constexpr (P == F16) return __half22float2(*(const __half2*)&w);
+  else if constexpr (P == I16) return i16x2_to_float2(w);
   else return __bfloat1622float2(*(const __nv_bfloat162*)&w);
 }
 
@@ -99,9 +101,10 @@ __device__ __forceinline__ void center_combine(const HopParams& p, long long x_c
     }
   } else {
     float n0 = 1.0f, nu = 1.0f, nl = 1.0f;
-    if constexpr (P == F16) {
-      n0 = __ldg(f.norm + x_cb * W + col);
-      if (bid) { nu = __ldg(f.norm + x_cb * W + cu) * n.fu; nl = __ldg(f.norm + x_cb * W + cl) * n.fl; }
+    if constexpr (P == F16 || P == I16) {
+      const float u = P == I16 ? I16_INV : 1.0f;   // fixed-point unit
+      n0 = __ldg(f.norm + x_cb * W + col) * u;
+      if (bid) { nu = __ldg(f.norm + x_cb * W + cu) * n.fu * u; nl = __ldg(f.norm + x_cb * W + cl) * n.fl * u; }
     } else {
       nu = n.fu; nl = n.fl;
     }
@@ -175,9 +178,10 @@ __device__ __forceinline__ void hop_epilogue(const HopParams& p, typename PT<P>:
     __syncthreads();
   }
   // site pass: hc post(hop) + cc cop(center), |.|^2, then fin (column pass) or output
+  const float inv_w = 1.0f / (float)W, inv_ls = 1.0f / (float)Ls;
   for (int i = tid; i < nsites; i += nt) {
-    const int site_l = i / W, col = i - site_l * W;
-    const int r = col / Ls, s = col - r * Ls, grp = site_l * nrhs + r;
+    const int site_l = div_small(i, inv_w), col = i - site_l * W;
+    const int r = div_small(col, inv_ls), s = col - r * Ls, grp = site_l * nrhs + r;
     const long long x = site0 + site_l;
     double part = 0.0;
     if (x < p.x_end) {
@@ -219,8 +223,8 @@ __device__ __forceinline__ void hop_epilogue(const HopParams& p, typename PT<P>:
     }
     __syncthreads();
     for (int i = tid; i < nsites; i += nt) {
-      const int site_l = i / W, col = i - site_l * W;
-      const int r = col / Ls, s = col - r * Ls, grp = site_l * nrhs + r;
+      const int site_l = div_small(i, inv_w), col = i - site_l * W;
+      const int r = div_small(col, inv_ls), s = col - r * Ls, grp = site_l * nrhs + r;
       const long long x = site0 + site_l;
       double part = 0.0;
       if (x < p.x_end) {

@@ -18,7 +18,7 @@
 
 namespace mdwf {
 
-enum Prec { F64 = 0, F32 = 1, F16 = 2, BF16 = 3 };
+enum Prec { F64 = 0, F32 = 1, F16 = 2, BF16 = 3, I16 = 4 };
 constexpr int MAXLS = 32;
 constexpr int MAXTHREADS = 256;  // threads per CTA of site-tiled kernels (NS * nrhs * Ls)
 
@@ -43,9 +43,27 @@ template <> struct PT<BF16> {
   static constexpr int NC = 3; static constexpr bool NORM = false;
   static constexpr int GS18 = 24, GS12 = 16;
 };
+// 16-bit fixed point: a site's reals are q / 32767 times its norm, links q / 32767
+template <> struct PT<I16> {
+  using C = float; using S = int16_t; using G = int16_t;
+  static constexpr int NC = 3; static constexpr bool NORM = true;
+  static constexpr int GS18 = 24, GS12 = 16;
+};
+constexpr float I16_ONE = 32767.0f;
+constexpr float I16_INV = 1.0f / 32767.0f;
+
+// the two int16 of a 32-bit word as exact floats: x + 1.5 2^23 written into a float's
+// mantissa (|x| < 2^22), minus 1.5 2^23
+__device__ __forceinline__ float2 i16x2_to_float2(uint32_t w) {
+  const int lo = (int)(int16_t)(w & 0xFFFFu), hi = (int)w >> 16;
+  return make_float2(__int_as_float(0x4B400000 + lo) - 12582912.0f, __int_as_float(0x4B400000 + hi) - 12582912.0f);
+}
+__device__ __forceinline__ uint32_t float2_to_i16x2(float a, float b) {
+  return ((uint32_t)(uint16_t)(int16_t)__float2int_rn(a)) | ((uint32_t)(uint16_t)(int16_t)__float2int_rn(b) << 16);
+}
 
 inline int prec_nc(int p) { return p == F64 ? 12 : p == F32 ? 6 : 3; }
-inline bool prec_norm(int p) { return p == F16; }
+inline bool prec_norm(int p) { return p == F16 || p == I16; }
 inline int gauge_stride(int p, int recon) {
   if (recon == 12) return p == F64 || p == F32 ? 12 : 16;
   return p == F64 ? 18 : p == F32 ? 20 : 24;
@@ -90,14 +108,15 @@ __device__ __forceinline__ void load_site(const Field& f, long long x_cb, int co
     const uint4* d = (const uint4*)f.data;
     float nrm = 1.0f;
     if constexpr (P == F16) nrm = __ldg(f.norm + x_cb * W + col);
+    if constexpr (P == I16) nrm = __ldg(f.norm + x_cb * W + col) * I16_INV;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
       uint4 q = __ldg(d + (x_cb * 3 + c) * W + col);
       const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
       for (int j = 0; j < 4; j++) {
-        if constexpr (P == F16) {
-          float2 fv = __half22float2(*(const __half2*)&w[j]);
+        if constexpr (P == F16 || P == I16) {
+          const float2 fv = P == F16 ? __half22float2(*(const __half2*)&w[j]) : i16x2_to_float2(w[j]);
           v[8 * c + 2 * j] = fv.x * nrm; v[8 * c + 2 * j + 1] = fv.y * nrm;
         } else {
           float2 fv = __bfloat1622float2(*(const __nv_bfloat162*)&w[j]);
@@ -125,7 +144,7 @@ __device__ __forceinline__ void store_site(const Field& f, long long x_cb, int c
   } else {
     uint4* d = (uint4*)f.data;
     float scale = 1.0f;
-    if constexpr (P == F16) {
+    if constexpr (P == F16 || P == I16) {
       float m = 0.0f;
 #pragma unroll
       for (int i = 0; i < 24; i++) m = fmaxf(m, fabsf(v[i]));
@@ -134,7 +153,7 @@ __device__ __forceinline__ void store_site(const Field& f, long long x_cb, int c
       // field they belong to
       if (!(m >= 1.17549435e-38f)) m = 0.0f;
       f.norm[x_cb * W + col] = m;
-      scale = m > 0.0f ? 1.0f / m : 0.0f;
+      scale = m > 0.0f ? (P == I16 ? I16_ONE : 1.0f) / m : 0.0f;
     }
 #pragma unroll
     for (int c = 0; c < 3; c++) {
@@ -144,6 +163,8 @@ __device__ __forceinline__ void store_site(const Field& f, long long x_cb, int c
         if constexpr (P == F16) {
           __half2 h = __floats2half2_rn(v[8 * c + 2 * j] * scale, v[8 * c + 2 * j + 1] * scale);
           w[j] = *(uint32_t*)&h;
+        } else if constexpr (P == I16) {
+          w[j] = float2_to_i16x2(v[8 * c + 2 * j] * scale, v[8 * c + 2 * j + 1] * scale);
         } else {
           __nv_bfloat162 h = __floats2bfloat162_rn(v[8 * c + 2 * j], v[8 * c + 2 * j + 1]);
           w[j] = *(uint32_t*)&h;
@@ -154,18 +175,48 @@ __device__ __forceinline__ void store_site(const Field& f, long long x_cb, int c
   }
 }
 
+// i / w for 0 <= i < 2^16, 1 <= w <= 2^10 without an integer division: the FP32 quotient
+// of i + 1/2 lies at least 1/(2w) from an integer and has a relative error below 2^-23
+// (checked exhaustively over that range).
+__device__ __forceinline__ int div_small(int i, float inv_w) { return __float2int_rz(((float)i + 0.5f) * inv_w); }
+
 // ---------------------------------------------------------------- geometry
+// n / d for 0 <= n < 2^32 by a multiply-high (Granlund-Montgomery, round-up variant):
+// m = floor(2^(32+l) / d) + 1 with l = ceil(log2 d) has m d - 2^(32+l) <= 2^l, so
+// floor(n m / 2^(32+l)) = floor(n / d); m < 2^33 is kept as m_hi 2^32 + m_lo.
+struct FastDiv {
+  uint32_t m_lo, m_hi, l;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f{0u, 1u, 0u};   // d = 1: m = 2^32
+  if (d > 1) {
+    uint32_t l = 0;
+    while ((1ull << l) < d) l++;
+    const unsigned long long m = ((1ull << (32 + l)) / d) + 1ull;
+    f.m_lo = (uint32_t)m;
+    f.m_hi = (uint32_t)(m >> 32);
+    f.l = l;
+  }
+  return f;
+}
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
+  const uint32_t t = __umulhi(n, f.m_lo);
+  return (uint32_t)(((unsigned long long)t + (f.m_hi ? n : 0u)) >> f.l);
+}
+
 struct Geom {
   int X, Y, Z, T, Xh;
-  long long vh;
+  long long vh;      // < 2^31
+  FastDiv fXh, fY, fZ;
 };
 
 __device__ __forceinline__ void cb_coords(const Geom& g, long long x_cb, int parity, int c[4]) {
-  int xh = (int)(x_cb % g.Xh);
-  long long rest = x_cb / g.Xh;
-  c[1] = (int)(rest % g.Y); rest /= g.Y;
-  c[2] = (int)(rest % g.Z);
-  c[3] = (int)(rest / g.Z);
+  const uint32_t n = (uint32_t)x_cb;
+  const uint32_t r1 = fdiv(n, g.fXh), r2 = fdiv(r1, g.fY), r3 = fdiv(r2, g.fZ);
+  const int xh = (int)(n - r1 * (uint32_t)g.Xh);
+  c[1] = (int)(r1 - r2 * (uint32_t)g.Y);
+  c[2] = (int)(r2 - r3 * (uint32_t)g.Z);
+  c[3] = (int)r3;
   c[0] = 2 * xh + ((parity + c[1] + c[2] + c[3]) & 1);
 }
 

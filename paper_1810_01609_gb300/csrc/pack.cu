@@ -9,6 +9,8 @@
 #include "mdwf_impl.cuh"
 #include "mdwf_kernels.h"
 
+#include <type_traits>
+
 namespace mdwf {
 
 __device__ __forceinline__ long long full_index(const Geom& g, const int c[4]) {
@@ -50,10 +52,11 @@ __global__ void pack_kernel(PackParams p) {
       d[(x_cb * 6 + k) * W + col] = make_float4(__double2float_rn(v[4 * k]), __double2float_rn(v[4 * k + 1]),
                                                 __double2float_rn(v[4 * k + 2]), __double2float_rn(v[4 * k + 3]));
   } else {
-    // F16: norm = float(max |v|), half = RNE(v / double(norm)); BF16: RNE(v)
+    // F16: norm = float(max |v|), half = RNE(v / double(norm)); BF16: RNE(v);
+    // I16: norm as F16, q = RNE(32767 v / double(norm)) (FP64 product, then quotient)
     double scale_div = 1.0;
     bool zero = false;
-    if constexpr (P == F16) {
+    if constexpr (P == F16 || P == I16) {
       double m = 0.0;
 #pragma unroll
       for (int k = 0; k < 24; k++) m = fmax(m, fabs(v[k]));
@@ -71,6 +74,8 @@ __global__ void pack_kernel(PackParams p) {
         if constexpr (P == F16) {
           __half q = zero ? __float2half(0.0f) : __double2half(v[8 * k + j] / scale_div);
           h[j] = *(uint16_t*)&q;
+        } else if constexpr (P == I16) {
+          h[j] = zero ? (uint16_t)0 : (uint16_t)(int16_t)__double2int_rn(32767.0 * v[8 * k + j] / scale_div);
         } else {
           __nv_bfloat16 q = __double2bfloat16(v[8 * k + j]);
           h[j] = *(uint16_t*)&q;
@@ -110,6 +115,7 @@ __global__ void unpack_kernel(PackParams p) {
     const uint4* d = (const uint4*)p.data[parity];
     double nrm = 1.0;
     if constexpr (P == F16) nrm = (double)p.norm[parity][x_cb * W + col];
+    if constexpr (P == I16) nrm = (double)p.norm[parity][x_cb * W + col] / 32767.0;
 #pragma unroll
     for (int k = 0; k < 3; k++) {
       uint4 q = d[(x_cb * 3 + k) * W + col];
@@ -118,6 +124,7 @@ __global__ void unpack_kernel(PackParams p) {
       for (int j = 0; j < 8; j++) {
         uint16_t b = (uint16_t)(w[j >> 1] >> (16 * (j & 1)));
         if constexpr (P == F16) v[8 * k + j] = (double)__half2float(*(__half*)&b) * nrm;
+        else if constexpr (P == I16) v[8 * k + j] = (double)(int16_t)b * nrm;
         else v[8 * k + j] = (double)__bfloat162float(*(__nv_bfloat16*)&b);
       }
     }
@@ -146,6 +153,7 @@ cudaError_t launch_pack(int prec, const PackParams& p, cudaStream_t st) {
     case F32: return go1d(pack_kernel<F32>, n, p, st);
     case F16: return go1d(pack_kernel<F16>, n, p, st);
     case BF16: return go1d(pack_kernel<BF16>, n, p, st);
+    case I16: return go1d(pack_kernel<I16>, n, p, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -157,6 +165,7 @@ cudaError_t launch_unpack(int prec, const PackParams& p, cudaStream_t st) {
     case F32: return go1d(unpack_kernel<F32>, n, p, st);
     case F16: return go1d(unpack_kernel<F16>, n, p, st);
     case BF16: return go1d(unpack_kernel<BF16>, n, p, st);
+    case I16: return go1d(unpack_kernel<I16>, n, p, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -246,6 +255,7 @@ __global__ void gauge_convert_kernel(const double* in, G* out, long long nlinks,
     const double v = k < nreal ? in[i * gs_in + k] : 0.0;
     if constexpr (sizeof(G) == 8) out[i * gs_out + k] = v;
     else if constexpr (sizeof(G) == 4) out[i * gs_out + k] = (float)v;
+    else if constexpr (std::is_same<G, int16_t>::value) out[i * gs_out + k] = (int16_t)__double2int_rn(32767.0 * v);
     else out[i * gs_out + k] = G(v);
   }
 }
@@ -258,6 +268,7 @@ cudaError_t launch_gauge_convert(int prec, const double* in64, void* out, long l
     case F32: gauge_convert_kernel<float><<<b, 128, 0, st>>>(in64, (float*)out, nlinks, gs_in, gs_out, nreal); break;
     case F16: gauge_convert_kernel<__half><<<b, 128, 0, st>>>(in64, (__half*)out, nlinks, gs_in, gs_out, nreal); break;
     case BF16: gauge_convert_kernel<__nv_bfloat16><<<b, 128, 0, st>>>(in64, (__nv_bfloat16*)out, nlinks, gs_in, gs_out, nreal); break;
+    case I16: gauge_convert_kernel<int16_t><<<b, 128, 0, st>>>(in64, (int16_t*)out, nlinks, gs_in, gs_out, nreal); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -46,6 +46,7 @@ cudaError_t launch_pack_face(int prec, int sig, const FaceParams& p, cudaStream_
     case F32: return launch_pf<F32>(sig, p, st);
     case F16: return launch_pf<F16>(sig, p, st);
     case BF16: return launch_pf<BF16>(sig, p, st);
+    case I16: return launch_pf<I16>(sig, p, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -222,6 +222,7 @@ cudaError_t launch_chain(int prec, const SLParams& p, cudaStream_t st) {
     case F32: return go(chain_kernel<F32>, p, W, smem, st);
     case F16: return go(chain_kernel<F16>, p, W, smem, st);
     case BF16: return go(chain_kernel<BF16>, p, W, smem, st);
+    case I16: return go(chain_kernel<I16>, p, W, smem, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -234,6 +235,7 @@ cudaError_t launch_axpby(int prec, const SLParams& p, cudaStream_t st) {
     case F32: return go(axpby_kernel<F32>, p, W, smem, st);
     case F16: return go(axpby_kernel<F16>, p, W, smem, st);
     case BF16: return go(axpby_kernel<BF16>, p, W, smem, st);
+    case I16: return go(axpby_kernel<I16>, p, W, smem, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -247,6 +249,7 @@ cudaError_t launch_cg_update(int prec_x, int prec, const SLParams& p, cudaStream
       case F32: return go(cg_update_kernel<F32, F32>, p, W, smem, st);
       case F16: return go(cg_update_kernel<F32, F16>, p, W, smem, st);
       case BF16: return go(cg_update_kernel<F32, BF16>, p, W, smem, st);
+      case I16: return go(cg_update_kernel<F32, I16>, p, W, smem, st);
     }
   }
   return cudaErrorInvalidValue;
@@ -260,6 +263,7 @@ cudaError_t launch_dot(int prec, const SLParams& p, cudaStream_t st) {
     case F32: return go(dot_kernel<F32>, p, W, smem, st);
     case F16: return go(dot_kernel<F16>, p, W, smem, st);
     case BF16: return go(dot_kernel<BF16>, p, W, smem, st);
+    case I16: return go(dot_kernel<I16>, p, W, smem, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -271,6 +275,7 @@ cudaError_t launch_rhs_axpy(int prec, const SLParams& p, cudaStream_t st) {
     case F32: return go(rhs_axpy_kernel<F32>, p, W, 0, st);
     case F16: return go(rhs_axpy_kernel<F16>, p, W, 0, st);
     case BF16: return go(rhs_axpy_kernel<BF16>, p, W, 0, st);
+    case I16: return go(rhs_axpy_kernel<I16>, p, W, 0, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -280,6 +285,7 @@ cudaError_t launch_convert(int po, int pi, const SLParams& p, cudaStream_t st) {
 #define CV(A, B) if (po == A && pi == B) return go(convert_kernel<A, B>, p, W, 0, st);
   CV(F64, F64) CV(F64, F32) CV(F64, F16) CV(F64, BF16)
   CV(F32, F64) CV(F16, F64) CV(BF16, F64) CV(F32, F32) CV(F16, F32) CV(BF16, F32)
+  CV(F64, I16) CV(I16, F64) CV(I16, F32)
 #undef CV
   return cudaErrorInvalidValue;
 }

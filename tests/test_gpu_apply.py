@@ -92,7 +92,7 @@ ALL_OPS = ["HOP_EO", "HOP_OE", "HOP_EO_DAG", "HOP_OE_DAG", "D5", "D5_DAG", "M5",
 
 
 @pytest.mark.parametrize("case", CASES)
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16", "i16"])
 def test_apply_parity(case, prec, monkeypatch):
     dims, Ls, nrhs = case
     if dims == (6, 2, 2, 6):
@@ -222,3 +222,43 @@ def test_pack_f16_bit_exact_and_roundtrip():
     got = to_host(back)
     assert np.array_equal(got.real, storage.round_bf16(psi.real))
     assert np.array_equal(got.imag, storage.round_bf16(psi.imag))
+
+
+def test_pack_i16_bit_exact_and_roundtrip():
+    """16-bit fixed point: the stored int16 and norms are the oracle's quantisation, and
+    unpacking gives the oracle's q * (norm / 32767) exactly."""
+    m = lib()
+    dims, Ls, nrhs = (4, 4, 2, 4), 4, 2
+    ctx = m.Context(dims, Ls)
+    psi = inputs.gaussian_spinor5d(dims, Ls, 8, nrhs=nrhs)
+    psi[0, 1, 0, 0, 0, 0] = 0.0        # an all-zero 5D site
+    psi[1, 2, 1] *= 1e-30              # tiny magnitudes
+    d = to_dev(psi)
+    buf = torch.zeros(ctx.field_bytes("i16", nrhs), dtype=torch.uint8, device="cuda")
+    m.mdwf_pack(ctx.h, d, buf, m.PRECS["i16"], nrhs)
+    raw = buf.cpu().numpy()
+    X, Y, Z, T = dims
+    par = parity_of(dims)
+    for parity in (0, 1):
+        h, n = _internal_half_f16(raw, ctx, nrhs, parity)   # same 16-bit layout
+        t, z, y, x = np.nonzero(par == parity)
+        order = np.argsort(((t * Z + z) * Y + y) * X + x)
+        t, z, y, x = t[order], z[order], y[order], x[order]
+        sites = psi[:, :, t, z, y, x]
+        reals = np.stack([sites.real, sites.imag], -1)
+        reals = np.transpose(reals, (2, 0, 1, 4, 3, 5)).reshape(len(t), nrhs, Ls, 24)
+        eq, en = storage.quantize_i16(reals)
+        assert np.array_equal(n, en)
+        assert np.array_equal(h.view(np.int16), eq)
+    back = torch.zeros_like(d)
+    m.mdwf_unpack(ctx.h, buf, back, m.PRECS["i16"], nrhs)
+    got = to_host(back)
+    for parity in (0, 1):
+        h, n = _internal_half_f16(raw, ctx, nrhs, parity)
+        t, z, y, x = np.nonzero(par == parity)
+        order = np.argsort(((t * Z + z) * Y + y) * X + x)
+        t, z, y, x = t[order], z[order], y[order], x[order]
+        ev = storage.dequantize_i16(h.view(np.int16), n).reshape(len(t), nrhs, Ls, 3, 4, 2)
+        ev = np.transpose(ev, (1, 2, 0, 4, 3, 5))           # [nrhs, Ls, vh, spin, colour, 2]
+        g = got[:, :, t, z, y, x]
+        assert np.array_equal(g.real, ev[..., 0]) and np.array_equal(g.imag, ev[..., 1])

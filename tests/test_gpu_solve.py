@@ -21,13 +21,13 @@ def _problem(dims=(4, 4, 4, 4), Ls=8, mf=0.05, eps=0.2, seed=1):
     return U, Ub, p, b, xo
 
 
-@pytest.mark.parametrize("sloppy", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("sloppy", ["f64", "f32", "f16", "bf16", "i16"])
 @pytest.mark.parametrize("use_graph", [False, True])
 @pytest.mark.parametrize("tc", ["0", "1"])
 def test_solve_matches_oracle(sloppy, use_graph, tc, monkeypatch):
     """tc: MDWF_TC=0 keeps the 16-bit hops on CUDA cores, 1 puts them on the tcgen05
     tensor-core kernel (the fused CG-iteration kernels included)."""
-    if tc == "1" and sloppy in ("f64", "f32"):
+    if tc == "1" and sloppy in ("f64", "f32", "i16"):
         pytest.skip("the tensor-core hop serves 16-bit storage only")
     monkeypatch.setenv("MDWF_TC", tc)
     m = lib()

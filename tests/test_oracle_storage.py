@@ -50,3 +50,28 @@ def test_bf16_rounding_cases():
         v, e = eval(v), eval(e)
         assert storage.round_bf16(np.array([v]))[0] == e, (v, e)
         assert int(storage.bf16_bits(np.array([v]))[0]) == int(bits, 16)
+
+
+def test_i16_rounding_cases():
+    """norm = 2 (site[0]); the value 2 v stores RNE(32767 v)."""
+    for v, e in _cases("i16"):
+        v, e = eval(v), int(e)
+        site = np.zeros(24)
+        site[0] = 2.0
+        site[7] = 2.0 * v
+        q, n = storage.quantize_i16(site)
+        assert n == np.float32(2.0) and q[0] == 32767
+        assert int(q[7]) == e, (v, int(q[7]), e)
+
+
+def test_i16_norm_zero_site_and_roundtrip_bound():
+    rng = np.random.default_rng(4)
+    v = rng.standard_normal((1000, 24))
+    v[3] = 0.0
+    q, n = storage.quantize_i16(v)
+    assert n[3] == 0.0 and not np.any(q[3])
+    assert np.all(np.abs(q).max(axis=-1)[n > 0] == 32767)     # the largest real maps to +-32767
+    back = storage.dequantize_i16(q, n)
+    # half a unit of 1/32767 of the norm (plus the float32 rounding of the norm)
+    bound = n.astype(np.float64)[:, None] * (0.5 / 32767 + 2.0 ** -23)
+    assert np.all(np.abs(back - v) <= bound)
