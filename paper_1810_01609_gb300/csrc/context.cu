@@ -75,7 +75,8 @@ struct mdwf_ctx {
   // reductions
   double* partials = nullptr;
   size_t partials_n = 0;
-  unsigned* counter = nullptr;
+  unsigned* counter = nullptr;       // grid-reduction counters: [0] and one per block group
+  size_t counters_n = 0;
   double* red_out = nullptr;   // device [256]
   double* red_host = nullptr;  // pinned [256]
   CGScalars* cg = nullptr;     // device [64]
@@ -212,18 +213,25 @@ size_t field_bytes_of(const Field& f, int prec) {
 // device, frees the old buffer and destroys every graph (they are re-captured on their
 // next use, whose first block of iterations runs eagerly and sizes the buffer first).
 int ensure_reduce(mdwf_ctx* c, long long blocks, int nrhs) {
-  const size_t need = (size_t)blocks * nrhs;
-  if (need > c->partials_n) {
+  const long long groups = (blocks + RED_GROUP - 1) / RED_GROUP;
+  const size_t need = (size_t)(blocks + groups) * nrhs;   // block partials, then group partials
+  if (need > c->partials_n || (size_t)groups + 1 > c->counters_n) {
     const size_t n = std::max(need, 2 * c->partials_n);
+    const size_t nc = std::max((size_t)groups + 1, 2 * c->counters_n);
     CK(cudaDeviceSynchronize());
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
     c->graphs.clear();
     c->graph_bytes.clear();
     if (c->partials) cudaFree(c->partials);
+    if (c->counter) cudaFree(c->counter);
     c->partials = nullptr;
-    c->partials_n = 0;
+    c->counter = nullptr;
+    c->partials_n = c->counters_n = 0;
     CK(cudaMalloc(&c->partials, n * sizeof(double)));
     c->partials_n = n;
+    CK(cudaMalloc(&c->counter, nc * sizeof(unsigned)));
+    CK(cudaMemset(c->counter, 0, nc * sizeof(unsigned)));
+    c->counters_n = nc;
   }
   return MDWF_SUCCESS;
 }
@@ -564,6 +572,7 @@ int hop(mdwf_ctx* c, int prec, bool dag, const Field& in, const Field& out, int 
     if (q.red.mode != RED_NONE) {
       CKS(ensure_reduce(c, blocks, in.nrhs));
       q.red.partials = c->partials;
+      q.red.counter = c->counter;
     }
     cudaError_t err = tc ? launch_hop_tc(prec, dag, r12, e.on, q, st)
                          : launch_hop(prec, dag, r12, e.on, (cfg & kOccBit) != 0, q, st);
@@ -621,6 +630,7 @@ int sl_axpby(mdwf_ctx* c, int prec, const Field* a, const Field& b, double ca, c
   if (red.mode != RED_NONE) {
     CKS(ensure_reduce(c, blocks, b.nrhs));
     p.red.partials = c->partials;
+    p.red.counter = c->counter;
   }
   cudaError_t err = launch_axpby(prec, p, st);
   c->launches++;
@@ -675,6 +685,7 @@ int dot(mdwf_ctx* c, int prec, const Field& a, const Field& b, std::vector<doubl
   p.ns = ns_default(W);
   CKS(ensure_reduce(c, (c->vh + p.ns - 1) / p.ns, a.nrhs));
   p.red.partials = c->partials;
+  p.red.counter = c->counter;
   cudaError_t err = launch_dot(prec, p, st);
   c->launches++;
   c->bytes += 2.0 * half_bytes(a, prec);
@@ -1365,9 +1376,7 @@ void mdwf_destroy(mdwf_ctx* c) {
 }
 
 static int ensure_small(mdwf_ctx* c) {
-  if (c->counter) return MDWF_SUCCESS;
-  CK(cudaMalloc(&c->counter, sizeof(unsigned)));
-  CK(cudaMemset(c->counter, 0, sizeof(unsigned)));
+  if (c->red_out) return MDWF_SUCCESS;
   CK(cudaMalloc(&c->red_out, 256 * sizeof(double)));
   CK(cudaMalloc(&c->cg, 64 * sizeof(CGScalars)));
   CK(cudaMemset(c->cg, 0, 64 * sizeof(CGScalars)));

@@ -410,17 +410,40 @@ template <typename C> __device__ __forceinline__ C pick(float f, double d) {
 
 struct Red {
   int mode;
-  double* partials;
-  unsigned int* counter;
+  double* partials;   // [blocks][nrhs] block partials, then [groups][nrhs] group partials
+  unsigned int* counter;   // [0]: groups finished; [1 + g]: blocks of group g finished
   double* out;        // RED_STORE: out[r]
   CGScalars* cg;      // RED_CG_*
   int nrhs;
 };
 
+constexpr int RED_GROUP = 128;   // blocks per first-level group of the grid reduction
+
+// fixed-order sum over i < n of src[i * stride] by the whole block (sm: blockDim doubles)
+__device__ inline double block_sum_strided(const double* src, int n, int stride, double* sm) {
+  const int tid = threadIdx.x;
+  double acc = 0.0;
+  for (int b = tid; b < n; b += blockDim.x) acc += __ldcg(src + (long long)b * stride);
+  sm[tid] = acc;
+  __syncthreads();
+  for (int w = blockDim.x; w > 1;) {
+    const int h = (w + 1) >> 1;
+    if (tid < w - h) sm[tid] += sm[tid + h];
+    __syncthreads();
+    w = h;
+  }
+  const double tot = sm[0];
+  __syncthreads();
+  return tot;
+}
+
 // Grid reduction of per-5D-site values sm[(site_l * nrhs + r) * Ls + s], i < ns * nrhs * Ls,
 // already in shared memory (scratch must hold max(ns*nrhs*Ls, blockDim.x) + ns*nrhs doubles):
-// fixed-order sums per (site, rhs), per rhs over the block, then the last block to finish
-// sums the block partials in a fixed order and runs the scalar program.
+// fixed-order sums per (site, rhs), per rhs over the block; the last block of each group of
+// RED_GROUP blocks sums its group's partials, the last group to finish sums the group
+// partials and runs the scalar program.  Every sum runs in a fixed order, whichever block
+// finishes last: the result is deterministic, and no block reads more than
+// max(RED_GROUP, blocks / RED_GROUP) partials per right-hand side.
 __device__ inline void block_grid_reduce_sm(const Red& red, double* sm, int Ls, int ns) {
   const int tid = threadIdx.x;
   const int nrhs = red.nrhs;
@@ -439,28 +462,33 @@ __device__ inline void block_grid_reduce_sm(const Red& red, double* sm, int Ls, 
     for (int i = 0; i < ns; i++) acc += sm2[i * nrhs + r];
     red.partials[(long long)blockIdx.x * nrhs + r] = acc;
   }
+  const int nb = gridDim.x;
+  const int g = blockIdx.x / RED_GROUP, ngroups = (nb + RED_GROUP - 1) / RED_GROUP;
+  const int gsize = min(RED_GROUP, nb - g * RED_GROUP);
+  double* gpart = red.partials + (long long)nb * nrhs;
   __shared__ unsigned int ticket;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) ticket = atomicAdd(red.counter + 1 + g, 1u);
+  __syncthreads();
+  if (ticket != (unsigned)gsize - 1) return;
+  __threadfence();
+  // last block of group g: its group's partials, fixed order
+  for (int r = 0; r < nrhs; r++) {
+    const double tot = block_sum_strided(red.partials + ((long long)g * RED_GROUP) * nrhs + r, gsize, nrhs, sm);
+    if (tid == 0) gpart[(long long)g * nrhs + r] = tot;
+  }
+  if (tid == 0) red.counter[1 + g] = 0u;
   __threadfence();
   __syncthreads();
   if (tid == 0) ticket = atomicAdd(red.counter, 1u);
   __syncthreads();
-  if (ticket != gridDim.x - 1) return;
+  if (ticket != (unsigned)ngroups - 1) return;
   __threadfence();
-  // last block: fixed-order sums over blocks
-  const int nb = gridDim.x;
+  // last group: the group partials, fixed order, and the scalar program
   for (int r = 0; r < nrhs; r++) {
-    double acc = 0.0;
-    for (int b = tid; b < nb; b += blockDim.x) acc += __ldcg(red.partials + (long long)b * nrhs + r);
-    sm[tid] = acc;
-    __syncthreads();
-    for (int w = blockDim.x; w > 1;) {
-      int h = (w + 1) >> 1;
-      if (tid < w - h) sm[tid] += sm[tid + h];
-      __syncthreads();
-      w = h;
-    }
+    const double tot = block_sum_strided(gpart + r, ngroups, nrhs, sm);
     if (tid == 0) {
-      const double tot = sm[0];
       if (red.mode == RED_STORE) {
         red.out[r] = tot;
       } else if (red.mode == RED_CG_ALPHA) {
@@ -486,7 +514,6 @@ __device__ inline void block_grid_reduce_sm(const Red& red, double* sm, int Ls, 
         c.beta_f = (float)c.beta;
       }
     }
-    __syncthreads();
   }
   if (tid == 0) *red.counter = 0u;
 }
