@@ -68,8 +68,8 @@ struct mdwf_ctx {
   long long vh;
   double alpha5, beta5;
   // gauge: [prec][parity]
-  void* gauge[4][2] = {};
-  int gs[4] = {};
+  void* gauge[NPREC][2] = {};   // [storage precision][parity]
+  int gs[NPREC] = {};
   bool gauge_loaded = false;
   std::map<std::string, DevBuf> ws;
   // reductions
@@ -1362,7 +1362,7 @@ void mdwf_destroy(mdwf_ctx* c) {
   if (!c) return;
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
   for (auto& kv : c->ws) if (kv.second.p) cudaFree(kv.second.p);
-  for (int p = 0; p < 4; p++)
+  for (int p = 0; p < NPREC; p++)
     for (int q = 0; q < 2; q++) if (c->gauge[p][q]) cudaFree(c->gauge[p][q]);
   if (c->partials) cudaFree(c->partials);
   if (c->counter) cudaFree(c->counter);
@@ -1402,7 +1402,7 @@ int mdwf_load_gauge(mdwf_ctx* c, const double* links, int where, void* stream) {
     CK(cudaMemcpyAsync(p, links, ubytes, cudaMemcpyHostToDevice, st));
     dev = (const double*)p;
   }
-  for (int p = 0; p < 4; p++)
+  for (int p = 0; p < NPREC; p++)
     for (int q = 0; q < 2; q++)
       if (c->gauge[p][q]) { cudaFree(c->gauge[p][q]); c->gauge[p][q] = nullptr; }
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);

@@ -19,6 +19,7 @@
 namespace mdwf {
 
 enum Prec { F64 = 0, F32 = 1, F16 = 2, BF16 = 3, I16 = 4 };
+constexpr int NPREC = 5;   // storage precisions (array extent for per-precision state)
 constexpr int MAXLS = 32;
 constexpr int MAXTHREADS = 256;  // threads per CTA of site-tiled kernels (NS * nrhs * Ls)
 
