@@ -41,13 +41,13 @@ WORKLOADS = {
     "48^3x96_Ls8": ((48, 48, 48, 96), 8, 0.005, 0.6, 5),
 }
 # extra modes (one JSON line each, not the default benchmark line)
-MODES = ("batch32", "large48", "graphbatch")
+MODES = ("batch32", "large48", "graphbatch", "multirhs")
 METRIC = "MDWF Dslash HBM GB/s (% of peak); solve time to 1e-10, mixed vs FP64"
 
 
 # the files that define the device code and launch of the hop kernels (the roofline kernel)
-KERNEL_FILES = ["dslash.cu", "dslash_bf16.cu", "dslash_f16.cu", "dslash_f32.cu", "dslash_f64.cu", "dslash_impl.cuh",
-                "mdwf_epi.cuh", "mdwf_impl.cuh", "mdwf_kernels.h"]
+KERNEL_FILES = ["dslash.cu", "dslash_bf16.cu", "dslash_f16.cu", "dslash_f32.cu", "dslash_f64.cu", "dslash_i16.cu",
+                "dslash_impl.cuh", "dslash_umma.cu", "mdwf_epi.cuh", "mdwf_impl.cuh", "mdwf_kernels.h"]
 
 
 def kernel_sources_hash():
@@ -367,6 +367,42 @@ def mode_batch32(args):
     print(json.dumps(out))
 
 
+def mode_multirhs(args):
+    """16^3x32, Ls 12: the 12 spin-colour point-source propagator solves with 1, 3, 6 and
+    12 right-hand sides per mdwf_solve_multi launch (after one warm-up pass per grouping:
+    tuning, graph capture); per-solve wall time, iterations and worst true residual."""
+    torch, m, stream = _setup_gpu()
+    import inputs
+    dims, Ls, mf, eps, seed = WORKLOADS["16^3x32_Ls12"]
+    ctx = m.Context(dims, Ls, mf=mf)
+    ctx.load_gauge(inputs.gauge_links(dims, eps, seed))
+    b4 = torch.stack([torch.from_numpy(inputs.point_source4d(dims, k // 3, k % 3)) for k in range(12)]).cuda()
+    eta = ctx.make_source_4d(b4, nrhs=12, stream=stream)
+    res = {}
+    for G in (1, 3, 6, 12):
+        def run():
+            its, worst = [], 0.0
+            for g0 in range(0, 12, G):
+                _, infos = ctx.solve_multi(eta[g0:g0 + G].contiguous(), sloppy=args.sloppy, tol=1e-10, stream=stream)
+                its += [i.iterations for i in infos]
+                worst = max(worst, max(i.true_residual for i in infos))
+            return its, worst
+        run()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its, worst = run()
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3
+        res[str(G)] = {"ms_per_solve": ms / 12, "iterations": [min(its), max(its)], "max_true_residual": worst}
+    out = {"metric": METRIC, "value": 12 / (min(r["ms_per_solve"] for r in res.values()) * 12e-3), "unit": "solves/s",
+           "n_gpus": 1, "steps": 1, "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f16+f32 (inner), f64", "data": "synthetic",
+           "config": {"workload": "multirhs: 16^3x32 Ls12, 12 point sources, 1/3/6/12 right-hand sides per launch",
+                      "lattice": list(dims), "Ls": Ls, "mf": mf, "sloppy": args.sloppy, "tol": 1e-10},
+           "per_launch_grouping": res}
+    print(json.dumps(out))
+
+
 def mode_large48(args):
     """48^3x96, Ls 8, m 0.005: one point-source mixed solve (links drawn on the device)."""
     torch, m, stream = _setup_gpu()
@@ -485,10 +521,12 @@ def main():
         return
     if args.impl == "reference":
         if wl in MODES:
-            wl = {"batch32": "32^3x64_Ls12", "large48": "48^3x96_Ls8", "graphbatch": "16^3x32_Ls12"}[wl]
+            wl = {"batch32": "32^3x64_Ls12", "large48": "48^3x96_Ls8", "graphbatch": "16^3x32_Ls12",
+                  "multirhs": "16^3x32_Ls12"}[wl]
         return run_reference(args, wl)
     if wl in MODES:
-        return {"batch32": mode_batch32, "large48": mode_large48, "graphbatch": mode_graphbatch}[wl](args)
+        return {"batch32": mode_batch32, "large48": mode_large48, "graphbatch": mode_graphbatch,
+                "multirhs": mode_multirhs}[wl](args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -588,6 +626,11 @@ def main():
         b.synchronize()
         kt.append(a.elapsed_time(b))
     kms = float(np.mean(kt))
+    # the configuration the autotuner chose for this kernel (sites per CTA; flags 65536:
+    # 64-register build, 131072: tensor-core kernel)
+    rk = [(k, v) for k, v, _ in ctx.tune_entries()
+          if k.startswith("hop|") and k.endswith("|p%d|epi2000" % prec) and "|n1|" in k]
+    roof_cfg = {"tune_key": rk[0][0], "tune_value": rk[0][1]} if rk else None
     vh = V // 2
     site = {"f16": 52.0, "bf16": 48.0, "f32": 96.0, "i16": 52.0}[args.sloppy]
     link = {"f16": 2, "bf16": 2, "f32": 4, "i16": 2}[args.sloppy] * 18.0
@@ -623,6 +666,17 @@ def main():
     e2e_ms = ee0.elapsed_time(ee1) / args.steps
     e2e_val = world * (ctx.algorithmic_bytes() - e2e_bytes0) / args.steps / (e2e_ms * 1e-3) / 1e9
     b4b, b5b = b4h.numel() * 16, eta_h.numel() * 16
+    # the same pinned 5D buffer copied by torch alone, both ways: the link's own speed
+    dtmp = torch.empty(sh5, dtype=torch.complex128, device="cuda")
+    c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    c0.record(stream)
+    dtmp.copy_(eta_h, non_blocking=True)
+    c1.record(stream)
+    eta_h.copy_(dtmp, non_blocking=True)
+    c2.record(stream)
+    torch.cuda.synchronize()
+    pinned_gbs = {"h2d": b5b / (c0.elapsed_time(c1) * 1e-3) / 1e9, "d2h": b5b / (c1.elapsed_time(c2) * 1e-3) / 1e9}
+    del dtmp
     e2e_h2d = b4b + 2 * b5b      # source (make_source_4d), 5D source (solve), 5D solution (project_4d)
     e2e_d2h = 2 * b5b + b4b      # 5D source, 5D solution, 4D propagator column
     del eta_h, x_h
@@ -659,12 +713,13 @@ def main():
         "roofline": {"kernel": "fused hop + M5^-1 (HOP_OE_M5INV, %s)" % args.sloppy, "bound": "hbm",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": stored_traffic("%s/HOP_OE_M5INV/%s" % (wl, args.sloppy)),
-                     "bytes_per_launch": kbytes, "ms_per_launch": kms},
+                     "bytes_per_launch": kbytes, "ms_per_launch": kms, "launch_config": roof_cfg},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "GB/s", "ms_per_step": e2e_ms,
                 "path": "mdwf_make_source_4d / mdwf_solve / mdwf_project_4d with pinned HOST pointers",
                 "true_residual": ih.true_residual,
-                "h2d_bytes_per_step": int(e2e_h2d), "d2h_bytes_per_step": int(e2e_d2h)},
+                "h2d_bytes_per_step": int(e2e_h2d), "d2h_bytes_per_step": int(e2e_d2h),
+                "pinned_copy_gbs_torch": pinned_gbs},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
