@@ -47,6 +47,7 @@ METRIC = "MDWF Dslash HBM GB/s (% of peak); solve time to 1e-10, mixed vs FP64"
 
 # the files that define the device code and launch of the hop kernels (the roofline kernel)
 KERNEL_FILES = ["dslash.cu", "dslash_bf16.cu", "dslash_f16.cu", "dslash_f32.cu", "dslash_f64.cu", "dslash_i16.cu",
+                "dslash2_bf16.cu", "dslash2_f16.cu", "dslash2_f32.cu", "dslash2_i16.cu",
                 "dslash_impl.cuh", "dslash_umma.cu", "mdwf_epi.cuh", "mdwf_impl.cuh", "mdwf_kernels.h"]
 
 
@@ -63,15 +64,19 @@ def kernel_sources_hash():
     return h.hexdigest()
 
 
-def stored_traffic(key):
+def stored_traffic(key, tune_value=None):
     """DRAM bytes per launch from profiles/roofline_traffic.json if it was captured on the
-    current kernel sources, else None."""
+    current kernel sources and on the same kernel variant (the tuner value's flag bits:
+    single-column, 64-register, tensor-core or paired-column kernel), else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
             d = json.load(f)
         if d.get("sources_sha256") != kernel_sources_hash():
             return None
-        return d["entries"][key]["dram_bytes_per_launch"]
+        e = d["entries"][key]
+        if tune_value is not None and "tune_value" in e and (e["tune_value"] >> 16) != (tune_value >> 16):
+            return None
+        return e["dram_bytes_per_launch"]
     except Exception:
         return None
 
@@ -627,7 +632,7 @@ def main():
         kt.append(a.elapsed_time(b))
     kms = float(np.mean(kt))
     # the configuration the autotuner chose for this kernel (sites per CTA; flags 65536:
-    # 64-register build, 131072: tensor-core kernel)
+    # 64-register build, 131072: tensor-core kernel, 262144: paired-column kernel)
     rk = [(k, v) for k, v, _ in ctx.tune_entries()
           if k.startswith("hop|") and k.endswith("|p%d|epi2000" % prec) and "|n1|" in k]
     roof_cfg = {"tune_key": rk[0][0], "tune_value": rk[0][1]} if rk else None
@@ -712,7 +717,8 @@ def main():
                   "speedup_vs_fp64": (fp64["ms"] / mixed_ms) if fp64 else None},
         "roofline": {"kernel": "fused hop + M5^-1 (HOP_OE_M5INV, %s)" % args.sloppy, "bound": "hbm",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": stored_traffic("%s/HOP_OE_M5INV/%s" % (wl, args.sloppy)),
+                     "frac": achieved / peak, "traffic": stored_traffic("%s/HOP_OE_M5INV/%s" % (wl, args.sloppy),
+                                                              roof_cfg["tune_value"] if roof_cfg else None),
                      "bytes_per_launch": kbytes, "ms_per_launch": kms, "launch_config": roof_cfg},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "GB/s", "ms_per_step": e2e_ms,

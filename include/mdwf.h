@@ -290,8 +290,8 @@ double mdwf_algorithmic_bytes(const mdwf_ctx* ctx);
  * t_ranks > 1 holds dims[3] timeslices of the global lattice.  Every hop it applies packs
  * the two faces of its input half -- per site of its first and of its last timeslice
  * and per column, the 12 reals of the half spinor (1 -/+ sig gamma_4) psi the receiving
- * hop needs, in the compute type (double for F64, float otherwise), followed for F16 by
- * one float norm per site and column -- launches the interior timeslices, calls the face
+ * hop needs, in the compute type (double for F64, float otherwise), followed for F16 and
+ * int16 by one float scale per site and column -- launches the interior timeslices, calls the face
  * exchange, then launches the first and last timeslices, which take their t neighbours
  * across the boundary from the received faces.  The result is bit-identical to the
  * undecomposed operator's.  Operators whose kernels reduce over the lattice (the CG

@@ -281,11 +281,12 @@ void load_tune(mdwf_ctx* c) {
     char* end = nullptr;
     e.ns = (int)strtol(line.c_str() + n0 + 5, &end, 10);
     // corrupt entry: ignore (valid: 1..64 sites per CTA, optionally with one of the hop
-    // kernels' flags 1 << 16 (occupancy-bounded build) or 1 << 17 (tensor-core kernel); a
-    // value no candidate list holds is ignored later too)
+    // kernels' flags 1 << 16 (occupancy-bounded build), 1 << 17 (tensor-core kernel) or
+    // 1 << 18 (paired-column kernel); a value no candidate list holds is ignored later too)
     const int ns_only = e.ns & 0xFFFF;
     const int flags = e.ns >> 16;
-    if (end == line.c_str() + n0 + 5 || e.ns <= 0 || ns_only <= 0 || ns_only > 64 || flags > 2) continue;
+    if (end == line.c_str() + n0 + 5 || e.ns <= 0 || ns_only <= 0 || ns_only > 64 ||
+        (flags != 0 && flags != 1 && flags != 2 && flags != 4)) continue;
     e.ms = strtod(line.c_str() + m0 + 5, nullptr);
     c->tune[line.substr(q0 + 1, q1 - q0 - 1)] = e;
   }
@@ -298,22 +299,30 @@ bool capturing(cudaStream_t st) {
 }
 
 // tuner value flags of the hop kernels (sites per CTA in the low 16 bits): the
-// occupancy-bounded build of the CUDA-core kernel, and the tcgen05 tensor-core kernel
+// occupancy-bounded build of the CUDA-core kernel, the tcgen05 tensor-core kernel, and the
+// paired-column CUDA-core kernel
 constexpr int kOccBit = 1 << 16;
 constexpr int kTcBit = 1 << 17;
+constexpr int kPairBit = 1 << 18;
 
 // Pick sites-per-CTA for `key` by brute force over `cands`, timing each with events.
 // In-place outputs listed in `snaps` are saved before and restored after every trial run,
 // so tuning does not change the result of the call.
+// MDWF_FORCE_NS pins the tuner value (sites per CTA, optionally with a kernel flag) where a
+// candidate list holds it; tests use it to exercise ragged last tiles and every kernel
+bool forced_cfg(const std::vector<int>& cands, int* out) {
+  const char* fns = getenv("MDWF_FORCE_NS");
+  if (!fns) return false;
+  const int f = atoi(fns);
+  for (int v : {f, f | kTcBit})
+    if (std::find(cands.begin(), cands.end(), v) != cands.end()) { *out = v; return true; }
+  return false;
+}
+
 template <typename F>
 int tuned_ns(mdwf_ctx* c, const std::string& key, const std::vector<int>& cands, int dflt,
              const std::vector<Snap>& snaps, cudaStream_t st, F run, int* ns_out) {
-  // MDWF_FORCE_NS pins sites-per-CTA (tests use it to exercise ragged last tiles)
-  if (const char* fns = getenv("MDWF_FORCE_NS")) {
-    const int f = atoi(fns);
-    for (int v : {f, f | kTcBit})
-      if (std::find(cands.begin(), cands.end(), v) != cands.end()) { *ns_out = v; return MDWF_SUCCESS; }
-  }
+  if (forced_cfg(cands, ns_out)) return MDWF_SUCCESS;
   auto it = c->tune.find(key);
   if (it != c->tune.end()) {
     if (std::find(cands.begin(), cands.end(), it->second.ns) != cands.end()) {
@@ -423,11 +432,12 @@ std::string chain_sig(const SChain& ch) {
   return s;
 }
 
-// bytes of one face: 12 compute-type reals per face site and column, then (F16) a norm
+// bytes of one face: 12 compute-type reals per face site and column, then (F16, int16) a
+// scale
 size_t face_bytes_of(const mdwf_ctx* c, int prec, int nrhs) {
   const size_t W = (size_t)nrhs * c->Ls;
   const size_t data = (size_t)c->slice_vh * W * 12 * (prec == F64 ? 8 : 4);
-  return ((data + 255) & ~(size_t)255) + (prec == F16 ? (size_t)c->slice_vh * W * 4 : 0);
+  return ((data + 255) & ~(size_t)255) + (prec == F16 || prec == I16 ? (size_t)c->slice_vh * W * 4 : 0);
 }
 
 // One hop on a T-partitioned lattice: pack the input half's two faces, launch the interior
@@ -448,7 +458,7 @@ int hop_partitioned(mdwf_ctx* c, int prec, bool dag, bool r12, bool epi, const H
     for (int k = 0; k < 4; k++) CKS(ws_get(c, names[k], fb, &buf[k]));
   }
   auto norm_of = [&](void* b) -> float* {
-    return prec == F16 ? (float*)((char*)b + ((fdata + 255) & ~(size_t)255)) : nullptr;
+    return prec == F16 || prec == I16 ? (float*)((char*)b + ((fdata + 255) & ~(size_t)255)) : nullptr;
   };
   const int SF = dag ? -1 : 1;
   FaceParams fp;
@@ -468,7 +478,7 @@ int hop_partitioned(mdwf_ctx* c, int prec, bool dag, bool r12, bool epi, const H
     q.x_begin = x0; q.x_end = x1;
     q.face_mode = mode; q.face = face; q.face_norm = face ? norm_of(face) : nullptr; q.face_base = base;
     cudaError_t err = tc ? launch_hop_tc(prec, dag, r12, epi, q, st)
-                         : launch_hop(prec, dag, r12, epi, (cfg & kOccBit) != 0, q, st);
+                         : launch_hop(prec, dag, r12, epi, (cfg & kOccBit) != 0, (cfg & kPairBit) != 0, q, st);
     c->launches++;
     if (err != cudaSuccess) { set_err("launch_hop", err); return MDWF_ERR_CUDA; }
     return MDWF_SUCCESS;
@@ -526,6 +536,16 @@ int hop(mdwf_ctx* c, int prec, bool dag, const Field& in, const Field& out, int 
       // fused 32-bit kernels also come in an occupancy-bounded build (tuner value | kOccBit)
       if (e.on && prec != F64) cands.push_back(ns | kOccBit);
     }
+    // the paired-column kernel: two columns per thread, ns * W / 2 threads
+    HopParams q = p;
+    q.ns = 1;
+    if (hop_pair_supported(prec, q)) {
+      for (int ns = 1; ns <= 64 && ns * W / 2 <= MAXTHREADS; ns++) {
+        q.ns = ns;
+        if (hop_smem_bytes(prec, q, e.on, true) > 200 * 1024) continue;
+        cands.push_back(ns | kPairBit);
+      }
+    }
   }
   if (tc_ok) {
     for (int ns = 1; ns <= 16; ns *= 2) {
@@ -559,7 +579,9 @@ int hop(mdwf_ctx* c, int prec, bool dag, const Field& in, const Field& out, int 
     }
     int cfg = dflt;
     auto it = c->tune.find(key);
-    if (it != c->tune.end() && std::find(cands.begin(), cands.end(), it->second.ns) != cands.end()) cfg = it->second.ns;
+    if (!forced_cfg(cands, &cfg) && it != c->tune.end() &&
+        std::find(cands.begin(), cands.end(), it->second.ns) != cands.end())
+      cfg = it->second.ns;
     return hop_partitioned(c, prec, dag, r12, e.on, p, cfg, in, out, st);
   }
   auto run = [&](int cfg) -> int {
@@ -575,7 +597,7 @@ int hop(mdwf_ctx* c, int prec, bool dag, const Field& in, const Field& out, int 
       q.red.counter = c->counter;
     }
     cudaError_t err = tc ? launch_hop_tc(prec, dag, r12, e.on, q, st)
-                         : launch_hop(prec, dag, r12, e.on, (cfg & kOccBit) != 0, q, st);
+                         : launch_hop(prec, dag, r12, e.on, (cfg & kOccBit) != 0, (cfg & kPairBit) != 0, q, st);
     c->launches++;
     c->bytes += half_bytes(in, prec) + gauge_bytes(c, prec) + (q.has_center ? half_bytes(e.center, prec) : 0.0) +
                 (q.axpy_r ? 2.0 * half_bytes(e.raxpy, prec) : half_bytes(out, prec));

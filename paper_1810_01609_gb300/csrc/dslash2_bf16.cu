@@ -1,0 +1,6 @@
+// BF16-storage instantiations of the paired-column CUDA-core hop kernel (see dslash_impl.cuh).
+#include "dslash_impl.cuh"
+
+namespace mdwf {
+template cudaError_t launch_hop2_prec<BF16>(const HopParams&, bool, bool, bool, int, size_t, cudaStream_t);
+}  // namespace mdwf

@@ -30,55 +30,6 @@ struct cplx { C re, im; };
 #define ARE(sp, co) acc[2 * ((co) * 4 + (sp))]
 #define AIM(sp, co) acc[2 * ((co) * 4 + (sp)) + 1]
 
-template <int MU, int SIG, typename C>
-__device__ __forceinline__ void hop_dir(const C psi[24], const C U[18], C acc[24]) {
-  const C sg = (C)SIG;
-  cplx<C> h0[3], h1[3];
-#pragma unroll
-  for (int co = 0; co < 3; co++) {
-    if (MU == 0) {         // h0 = p0 - s i p3 ; h1 = p1 - s i p2
-      h0[co] = {PRE(0, co) + sg * PIM(3, co), PIM(0, co) - sg * PRE(3, co)};
-      h1[co] = {PRE(1, co) + sg * PIM(2, co), PIM(1, co) - sg * PRE(2, co)};
-    } else if (MU == 1) {  // h0 = p0 - s p3 ; h1 = p1 + s p2
-      h0[co] = {PRE(0, co) - sg * PRE(3, co), PIM(0, co) - sg * PIM(3, co)};
-      h1[co] = {PRE(1, co) + sg * PRE(2, co), PIM(1, co) + sg * PIM(2, co)};
-    } else if (MU == 2) {  // h0 = p0 - s i p2 ; h1 = p1 + s i p3
-      h0[co] = {PRE(0, co) + sg * PIM(2, co), PIM(0, co) - sg * PRE(2, co)};
-      h1[co] = {PRE(1, co) - sg * PIM(3, co), PIM(1, co) + sg * PRE(3, co)};
-    } else {               // h0 = p0 - s p2 ; h1 = p1 - s p3
-      h0[co] = {PRE(0, co) - sg * PRE(2, co), PIM(0, co) - sg * PIM(2, co)};
-      h1[co] = {PRE(1, co) - sg * PRE(3, co), PIM(1, co) - sg * PIM(3, co)};
-    }
-  }
-#pragma unroll
-  for (int a = 0; a < 3; a++) {
-    cplx<C> u0 = {0, 0}, u1 = {0, 0};
-#pragma unroll
-    for (int b = 0; b < 3; b++) {
-      const C ur = U[2 * (3 * a + b)], ui = U[2 * (3 * a + b) + 1];
-      u0.re += ur * h0[b].re - ui * h0[b].im;
-      u0.im += ur * h0[b].im + ui * h0[b].re;
-      u1.re += ur * h1[b].re - ui * h1[b].im;
-      u1.im += ur * h1[b].im + ui * h1[b].re;
-    }
-    ARE(0, a) += u0.re; AIM(0, a) += u0.im;
-    ARE(1, a) += u1.re; AIM(1, a) += u1.im;
-    if (MU == 0) {         // lower0 = s i Uh1 ; lower1 = s i Uh0
-      ARE(2, a) -= sg * u1.im; AIM(2, a) += sg * u1.re;
-      ARE(3, a) -= sg * u0.im; AIM(3, a) += sg * u0.re;
-    } else if (MU == 1) {  // lower0 = s Uh1 ; lower1 = -s Uh0
-      ARE(2, a) += sg * u1.re; AIM(2, a) += sg * u1.im;
-      ARE(3, a) -= sg * u0.re; AIM(3, a) -= sg * u0.im;
-    } else if (MU == 2) {  // lower0 = s i Uh0 ; lower1 = -s i Uh1
-      ARE(2, a) -= sg * u0.im; AIM(2, a) += sg * u0.re;
-      ARE(3, a) += sg * u1.im; AIM(3, a) -= sg * u1.re;
-    } else {               // lower0 = -s Uh0 ; lower1 = -s Uh1
-      ARE(2, a) -= sg * u0.re; AIM(2, a) -= sg * u0.im;
-      ARE(3, a) -= sg * u1.re; AIM(3, a) -= sg * u1.im;
-    }
-  }
-}
-
 // Load one link (18 reals, row-major [a][b] complex) in compute precision.
 template <int P, bool R12>
 __device__ __forceinline__ void load_link(const void* base, long long off, typename PT<P>::C U[18],
@@ -128,41 +79,59 @@ __device__ __forceinline__ void load_link(const void* base, long long off, typen
   }
 }
 
+// Explicitly rounded arithmetic on one value (float, double) or on a pair of columns
+// (float2, the packed FP32 instructions of sm_100+): the compiler makes no contraction
+// choices, so the single-column and the paired-column kernels perform the same roundings
+// in the same order and agree bit for bit.
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float vneg(float a) { return -a; }
+__device__ __forceinline__ double vmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double vfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ double vneg(double a) { return -a; }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
+
 // SU(3) on a projected half spinor h (2 slots x 3 colours, complex) and reconstruction:
-// upper spins += U h, lower spins += -sig X_mu^+ U h.
-template <int MU, int SIG, typename C>
-__device__ __forceinline__ void su3_recon(const C h[12], const C* U, C acc[24], const C n) {
-  const C sg = (C)SIG * n;   // the neighbour's storage scale folds into the accumulation
+// upper spins += n U h, lower spins += -sig n X_mu^+ U h, n the neighbour's storage scale.
+// V is the compute type, or float2 for two columns at once (U then holds every real twice).
+// Per output real: re = ((ur0 hr0 - ui0 hi0) + ur1 hr1 - ui1 hi1) + ..., one rounding per
+// product-add in this order.
+template <int MU, int SIG, typename V>
+__device__ __forceinline__ void su3_recon(const V h[12], const V* U, V acc[24], const V n) {
+  const V sg = SIG > 0 ? n : vneg(n);
+  const V nsg = vneg(sg);
 #pragma unroll
   for (int a = 0; a < 3; a++) {
-    cplx<C> u0, u1;
+    V u0r, u0i, u1r, u1i;
     {
-      const C ur = U[6 * a], ui = U[6 * a + 1];
-      u0.re = ur * h[0] - ui * h[1]; u0.im = ur * h[1] + ui * h[0];
-      u1.re = ur * h[6] - ui * h[7]; u1.im = ur * h[7] + ui * h[6];
+      const V ur = U[6 * a], ui = U[6 * a + 1], mui = vneg(ui);
+      u0r = vfma(mui, h[1], vmul(ur, h[0])); u0i = vfma(ui, h[0], vmul(ur, h[1]));
+      u1r = vfma(mui, h[7], vmul(ur, h[6])); u1i = vfma(ui, h[6], vmul(ur, h[7]));
     }
 #pragma unroll
     for (int b = 1; b < 3; b++) {
-      const C ur = U[2 * (3 * a + b)], ui = U[2 * (3 * a + b) + 1];
-      u0.re += ur * h[2 * b] - ui * h[2 * b + 1];
-      u0.im += ur * h[2 * b + 1] + ui * h[2 * b];
-      u1.re += ur * h[6 + 2 * b] - ui * h[6 + 2 * b + 1];
-      u1.im += ur * h[6 + 2 * b + 1] + ui * h[6 + 2 * b];
+      const V ur = U[2 * (3 * a + b)], ui = U[2 * (3 * a + b) + 1], mui = vneg(ui);
+      u0r = vfma(mui, h[2 * b + 1], vfma(ur, h[2 * b], u0r));
+      u0i = vfma(ui, h[2 * b], vfma(ur, h[2 * b + 1], u0i));
+      u1r = vfma(mui, h[6 + 2 * b + 1], vfma(ur, h[6 + 2 * b], u1r));
+      u1i = vfma(ui, h[6 + 2 * b], vfma(ur, h[6 + 2 * b + 1], u1i));
     }
-    ARE(0, a) += n * u0.re; AIM(0, a) += n * u0.im;
-    ARE(1, a) += n * u1.re; AIM(1, a) += n * u1.im;
+    ARE(0, a) = vfma(n, u0r, ARE(0, a)); AIM(0, a) = vfma(n, u0i, AIM(0, a));
+    ARE(1, a) = vfma(n, u1r, ARE(1, a)); AIM(1, a) = vfma(n, u1i, AIM(1, a));
     if (MU == 0) {         // lower0 = s i Uh1 ; lower1 = s i Uh0
-      ARE(2, a) -= sg * u1.im; AIM(2, a) += sg * u1.re;
-      ARE(3, a) -= sg * u0.im; AIM(3, a) += sg * u0.re;
+      ARE(2, a) = vfma(nsg, u1i, ARE(2, a)); AIM(2, a) = vfma(sg, u1r, AIM(2, a));
+      ARE(3, a) = vfma(nsg, u0i, ARE(3, a)); AIM(3, a) = vfma(sg, u0r, AIM(3, a));
     } else if (MU == 1) {  // lower0 = s Uh1 ; lower1 = -s Uh0
-      ARE(2, a) += sg * u1.re; AIM(2, a) += sg * u1.im;
-      ARE(3, a) -= sg * u0.re; AIM(3, a) -= sg * u0.im;
+      ARE(2, a) = vfma(sg, u1r, ARE(2, a)); AIM(2, a) = vfma(sg, u1i, AIM(2, a));
+      ARE(3, a) = vfma(nsg, u0r, ARE(3, a)); AIM(3, a) = vfma(nsg, u0i, AIM(3, a));
     } else if (MU == 2) {  // lower0 = s i Uh0 ; lower1 = -s i Uh1
-      ARE(2, a) -= sg * u0.im; AIM(2, a) += sg * u0.re;
-      ARE(3, a) += sg * u1.im; AIM(3, a) -= sg * u1.re;
+      ARE(2, a) = vfma(nsg, u0i, ARE(2, a)); AIM(2, a) = vfma(sg, u0r, AIM(2, a));
+      ARE(3, a) = vfma(sg, u1i, ARE(3, a)); AIM(3, a) = vfma(nsg, u1r, AIM(3, a));
     } else {               // lower0 = -s Uh0 ; lower1 = -s Uh1
-      ARE(2, a) -= sg * u0.re; AIM(2, a) -= sg * u0.im;
-      ARE(3, a) -= sg * u1.re; AIM(3, a) -= sg * u1.im;
+      ARE(2, a) = vfma(nsg, u0r, ARE(2, a)); AIM(2, a) = vfma(nsg, u0i, AIM(2, a));
+      ARE(3, a) = vfma(nsg, u1r, ARE(3, a)); AIM(3, a) = vfma(nsg, u1i, AIM(3, a));
     }
   }
 }
@@ -260,7 +229,7 @@ __device__ __forceinline__ typename PT<P>::C load_proj(const Field& f, unsigned 
 
 // The projected half spinor of a neighbour across the partition boundary, read from the
 // face the neighbouring partition packed (pack_face_kernel: the same 12 reals load_proj
-// forms, and for F16 the neighbour's norm).  nbr is the neighbour's index in the local
+// forms, and for F16 / int16 the neighbour's scale as load_proj returns it).  nbr is the neighbour's index in the local
 // lattice with periodic wrap, i.e. face_base + the face site.
 template <int P>
 __device__ __forceinline__ typename PT<P>::C load_face(const HopParams& p, unsigned nbr, int col,
@@ -271,7 +240,7 @@ __device__ __forceinline__ typename PT<P>::C load_face(const HopParams& p, unsig
   const C* src = (const C*)p.face + f * 12;
 #pragma unroll
   for (int k = 0; k < 12; k++) h[k] = src[k];
-  if constexpr (P == F16) return p.face_norm[f];
+  if constexpr (PT<P>::NORM) return p.face_norm[f];
   return (C)1;
 }
 
@@ -359,6 +328,129 @@ hop_kernel(const __grid_constant__ HopParams p) {
     __syncthreads();
     hop_epilogue<P>(p, tileH, redsm, p.ns);
   }
+}
+
+// Paired-column variant for the 32-bit compute types: thread (site_l, c) computes columns
+// c and c + W/2 of its site (W = nrhs * Ls even) on float2 = (column c, column c + W/2)
+// with the packed FP32 instructions, so one instruction stream carries two 5D sites and
+// each staged link real, loaded once as a duplicated pair, serves both.  Same roundings
+// in the same order as hop_kernel: the two kernels agree bit for bit.
+template <int P, bool DAG, bool R12, bool EPI>
+__global__ void __launch_bounds__(MAXTHREADS)
+hop2_kernel(const __grid_constant__ HopParams p) {
+  using C = float;
+  static_assert(P != F64, "paired columns: 32-bit compute types only");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Ls = p.in.Ls, nrhs = p.in.nrhs;
+  const int W = Ls * nrhs, W2 = W >> 1;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int site_l = tid / W2;
+  const int colA = tid - site_l * W2, colB = colA + W2;
+  const long long site0 = p.x_begin + (long long)blockIdx.x * p.ns;
+  const long long x_cb = site0 + site_l;
+  const bool active = x_cb < p.x_end;
+  constexpr int SF = DAG ? -1 : 1;
+  // shared: links as duplicated pairs (18 float2 = 144 bytes per link), neighbour table,
+  // epilogue
+  float2* slink = (float2*)smem_raw;
+  unsigned* snbr = (unsigned*)(slink + p.ns * 8 * 18);
+  unsigned char* epi_base = (unsigned char*)(snbr + ((p.ns * 8 + 3) & ~3));
+
+  for (int i = tid; i < p.ns * 8; i += nt) {
+    const long long x = site0 + (i >> 3);
+    if (x >= p.x_end) continue;
+    const int d = i & 7, mu = d & 3;
+    int c[4];
+    cb_coords(p.g, x, p.pout, c);
+    snbr[i] = (unsigned)nbr_cb(p.g, c, mu, d < 4 ? +1 : -1);
+    C U[18];
+    const bool flip = R12 && mu == 3 && p.t_bc < 0 &&
+                      (d < 4 ? c[3] == p.g.T - 1 && p.bc_hi : c[3] == 0 && p.bc_lo);
+    load_link<P, R12>(p.gauge, (x * 8 + d) * p.gs, U, flip);
+    float4* dst = (float4*)(slink + i * 18);
+#pragma unroll
+    for (int k = 0; k < 18; k += 2) dst[k >> 1] = make_float4(U[k], U[k], U[k + 1], U[k + 1]);
+  }
+  __syncthreads();
+
+  float2 acc[24];
+#pragma unroll
+  for (int i = 0; i < 24; i++) acc[i] = make_float2(0.0f, 0.0f);
+  if (active) {
+    const unsigned* nb = snbr + site_l * 8;
+    const float2* lk = slink + site_l * 8 * 18;
+    C hA[12], hB[12];
+    float2 h[12];
+#define HOP2_D(D, MU, SIG)                                                                \
+    { const bool fc = ((D) == 7 && p.face_mode == 1) || ((D) == 3 && p.face_mode == 2);    \
+      const C nA = fc ? load_face<P>(p, nb[D], colA, hA) : load_proj<P, MU, SIG>(p.in, nb[D], colA, hA); \
+      const C nB = fc ? load_face<P>(p, nb[D], colB, hB) : load_proj<P, MU, SIG>(p.in, nb[D], colB, hB); \
+      _Pragma("unroll") for (int k = 0; k < 12; k++) h[k] = make_float2(hA[k], hB[k]);     \
+      su3_recon<MU, SIG>(h, lk + (D) * 18, acc, make_float2(nA, nB)); }
+    HOP2_D(0, 0, SF) HOP2_D(4, 0, -SF) HOP2_D(1, 1, SF) HOP2_D(5, 1, -SF)
+    HOP2_D(2, 2, SF) HOP2_D(6, 2, -SF) HOP2_D(3, 3, SF) HOP2_D(7, 3, -SF)
+#undef HOP2_D
+  }
+
+  if constexpr (!EPI) {
+    if (active) {
+      C v[24];
+#pragma unroll
+      for (int k = 0; k < 24; k++) v[k] = acc[k].x;
+      store_site<P>(p.out, x_cb, colA, v);
+#pragma unroll
+      for (int k = 0; k < 24; k++) v[k] = acc[k].y;
+      store_site<P>(p.out, x_cb, colB, v);
+    }
+    return;
+  } else {
+    const int GS = tile_gstr(Ls);
+    const int ngrp = p.ns * nrhs;
+    C* tileH = (C*)epi_base;
+    const size_t toff = ((size_t)ngrp * GS * sizeof(C) + 15) & ~(size_t)15;
+    double* redsm = (double*)(epi_base + toff);
+    if (active) {
+      const int rA = colA / Ls, sA = colA - rA * Ls, rB = colB / Ls, sB = colB - rB * Ls;
+      C* dA = tileH + (site_l * nrhs + rA) * GS + sA * TSTR;
+      C* dB = tileH + (site_l * nrhs + rB) * GS + sB * TSTR;
+#pragma unroll
+      for (int k = 0; k < 24; k += 4) {
+        *(float4*)(dA + k) = make_float4(acc[k].x, acc[k + 1].x, acc[k + 2].x, acc[k + 3].x);
+        *(float4*)(dB + k) = make_float4(acc[k].y, acc[k + 1].y, acc[k + 2].y, acc[k + 3].y);
+      }
+    }
+    __syncthreads();
+    hop_epilogue<P>(p, tileH, redsm, p.ns);
+  }
+}
+
+template <int P, bool DAG, bool R12, bool EPI>
+static cudaError_t launch_pair(const HopParams& p, int threads, size_t smem, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(hop2_kernel<P, DAG, R12, EPI>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const long long blocks = (p.x_end - p.x_begin + p.ns - 1) / p.ns;
+  HopParams q = p;
+  q.hcf = (float)p.hc; q.ccf = (float)p.cc; q.mff = (float)p.mf;
+  hop2_kernel<P, DAG, R12, EPI><<<(unsigned)blocks, threads, smem, st>>>(q);
+  return cudaGetLastError();
+}
+
+// all (dagger, 12-real links, epilogue) variants of the paired-column kernel of one
+// 32-bit storage precision
+template <int P>
+cudaError_t launch_hop2_prec(const HopParams& p, bool dag, bool r12, bool epi, int threads, size_t smem,
+                             cudaStream_t st) {
+  if (dag) {
+    if (r12) return epi ? launch_pair<P, true, true, true>(p, threads, smem, st) : launch_pair<P, true, true, false>(p, threads, smem, st);
+    return epi ? launch_pair<P, true, false, true>(p, threads, smem, st) : launch_pair<P, true, false, false>(p, threads, smem, st);
+  }
+  if (r12) return epi ? launch_pair<P, false, true, true>(p, threads, smem, st) : launch_pair<P, false, true, false>(p, threads, smem, st);
+  return epi ? launch_pair<P, false, false, true>(p, threads, smem, st) : launch_pair<P, false, false, false>(p, threads, smem, st);
 }
 
 template <int P, bool DAG, bool R12, bool EPI, bool OCC = false>

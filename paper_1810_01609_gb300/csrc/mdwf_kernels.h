@@ -44,14 +44,18 @@ struct HopParams {
   int bc_lo, bc_hi;
 };
 
-size_t hop_smem_bytes(int prec, const HopParams& p, bool epi);
-// occ: the occupancy-bounded build of a fused 32-bit kernel (ignored otherwise)
-cudaError_t launch_hop(int prec, bool dag, bool r12, bool epi, bool occ, const HopParams& p, cudaStream_t st);
+// pair: the paired-column kernel (32-bit compute types, nrhs * Ls even, ns * nrhs * Ls / 2
+// threads); occ: the occupancy-bounded build of a fused single-column 32-bit kernel
+size_t hop_smem_bytes(int prec, const HopParams& p, bool epi, bool pair = false);
+int hop_threads(const HopParams& p, bool pair);
+bool hop_pair_supported(int prec, const HopParams& p);
+cudaError_t launch_hop(int prec, bool dag, bool r12, bool epi, bool occ, bool pair, const HopParams& p,
+                       cudaStream_t st);
 
 // one face of a T-partitioned lattice (partition.cu): for every site f of the local
 // timeslice starting at checkerboard index `first` (slice_vh sites) and every column, the
 // 12 reals of (1 - sig gamma_4) in projected as the hop kernels project them, in the
-// compute type, at face[(f * W + col) * 12]; F16 also the site's norm at norm[f * W + col]
+// compute type, at face[(f * W + col) * 12]; F16 / int16 also the site's scale at norm[f * W + col]
 struct FaceParams {
   Field in;
   long long slice_vh, first;

@@ -6,7 +6,7 @@
 // (1 - sig gamma_4) psi: 12 reals per face site and column, 2x less than the spinor.  This
 // kernel forms them with the hop kernels' own projection (load_proj), so a face holds
 // exactly the reals the receiving kernel would have formed from the field itself (and the
-// F16 norm): the partitioned operator is bit-identical to the undecomposed one.
+// F16 / int16 scale): the partitioned operator is bit-identical to the undecomposed one.
 #include "dslash_impl.cuh"
 
 namespace mdwf {
@@ -26,7 +26,7 @@ __global__ void pack_face_kernel(const __grid_constant__ FaceParams p) {
   C* dst = (C*)p.face + i * 12;
 #pragma unroll
   for (int k = 0; k < 12; k++) dst[k] = h[k];
-  if constexpr (P == F16) p.norm[i] = nrm;
+  if constexpr (PT<P>::NORM) p.norm[i] = nrm;
 }
 
 template <int P>

@@ -140,6 +140,51 @@ def test_tensor_core_hop_matches_oracle(prec, force_ns, monkeypatch):
             assert site_rel(got, ref, keep) <= SITE_TOL[prec], (op, prec, case, "per site")
 
 
+PAIR_BIT = 1 << 18   # tuner value flag of the paired-column hop kernel
+PAIR_CASES = [((4, 4, 4, 4), 8, 1), ((6, 2, 2, 6), 6, 1), ((4, 4, 4, 8), 12, 12), ((4, 2, 2, 4), 10, 2)]
+PAIR_OPS = ["HOP_EO", "HOP_OE_DAG", "HOP_OE_M5INV", "MPC", "MPC_DAG", "MDAGM", "FULL_D", "FULL_D_DAG",
+            "MPC_SYM", "MPC_SYM_DAG"]
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16", "bf16", "i16"])
+@pytest.mark.parametrize("ns", [1, 3, 16])
+def test_paired_hop_matches_oracle_and_single_column(prec, ns, monkeypatch):
+    """The paired-column hop kernel (two columns per thread on packed FP32 pairs) on every
+    hop-based op: parity with the oracle, and bit-identical to the single-column kernel
+    with the same sites per CTA (same roundings in the same order).  Cases: several tiles,
+    ragged last tiles (3 and 16 sites per CTA on 72- and 32-site half lattices), 1..12 RHS."""
+    monkeypatch.setenv("MDWF_TC", "0")
+    for dims, Ls, nrhs in PAIR_CASES:
+        if ns * nrhs * Ls > 256:
+            continue      # more threads than a CTA of the single-column kernel takes
+        m, ctx, U, Ub, psi, p = _setup(dims, Ls, nrhs)
+        par = parity_of(dims)
+        for op in PAIR_OPS:
+            monkeypatch.setenv("MDWF_FORCE_NS", str(ns))
+            single = _gpu_apply(m, ctx, op, prec, psi, nrhs)
+            monkeypatch.setenv("MDWF_FORCE_NS", str(PAIR_BIT | ns))
+            got = _gpu_apply(m, ctx, op, prec, psi, nrhs)
+            ref = np.stack([_oracle(op, Ub, psi[r], p, par) for r in range(nrhs)])
+            keep = _mask(op, par, ref.shape)
+            assert rel(got, ref) <= TOL[prec], (op, prec, dims, Ls, nrhs)
+            assert site_rel(got, ref, keep) <= SITE_TOL[prec], (op, prec, dims, Ls, nrhs, "per site")
+            assert np.array_equal(got, single), (op, prec, dims, Ls, nrhs, float(np.abs(got - single).max()))
+
+
+def test_paired_hop_chosen_by_tuner_only_for_even_columns(monkeypatch):
+    """nrhs * Ls odd: the paired kernel is no candidate, a forced pair value falls back to
+    the tuner, and the result is still right."""
+    monkeypatch.setenv("MDWF_TC", "0")
+    monkeypatch.setenv("MDWF_FORCE_NS", str(PAIR_BIT | 4))
+    dims, Ls, nrhs = (4, 4, 4, 4), 5, 3
+    m, ctx, U, Ub, psi, p = _setup(dims, Ls, nrhs)
+    par = parity_of(dims)
+    got = _gpu_apply(m, ctx, "MPC", "f16", psi, nrhs)
+    ref = np.stack([_oracle("MPC", Ub, psi[r], p, par) for r in range(nrhs)])
+    assert rel(got, ref) <= TOL["f16"]
+    assert not any((v >> 18) & 1 for _, v, _ in ctx.tune_entries())
+
+
 @pytest.mark.parametrize("prec", ["f16", "bf16"])
 def test_tensor_core_hop_recon12(prec, monkeypatch):
     """12-real links (third row rebuilt in the tensor-core kernel's link-matrix build,

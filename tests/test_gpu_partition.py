@@ -1,8 +1,8 @@
 """T-partitioned operator on one GPU: the lattice split into 2 and 4 partitions in t,
 each a context driven by its own host thread and stream, faces exchanged in-process by
 the library; every operator's output is bit-identical to the undecomposed context's
-(same kernels, same reals at every site), for all storage precisions and for both the
-CUDA-core and the tcgen05 hop kernels."""
+(same kernels, same reals at every site), for all storage precisions and for the
+single-column, the paired-column and the tcgen05 hop kernels."""
 import numpy as np
 import pytest
 
@@ -26,10 +26,15 @@ def _whole(m, ctx, op, prec, psi, nrhs):
     return out
 
 
-@pytest.mark.parametrize("tc", ["0", "1"])
+PAIR_BIT = 1 << 18   # tuner value flag of the paired-column hop kernel
+
+
+@pytest.mark.parametrize("tc", ["0", "1", "pair"])
 @pytest.mark.parametrize("nparts,recon", [(2, 18), (4, 18), (2, 12)])
 def test_partitioned_operators_bit_identical(nparts, recon, tc, monkeypatch):
-    monkeypatch.setenv("MDWF_TC", tc)
+    """tc "pair": the partitions run the paired-column kernel, the undecomposed context the
+    single-column one (4 sites per CTA each)."""
+    monkeypatch.setenv("MDWF_TC", "0" if tc == "pair" else tc)
     monkeypatch.setenv("MDWF_TUNE", "0")
     m = lib()
     from paper_1810_01609_gb300.partition import PartitionedLattice
@@ -40,10 +45,14 @@ def test_partitioned_operators_bit_identical(nparts, recon, tc, monkeypatch):
     part = PartitionedLattice(dims, Ls, nparts, mf=mf, recon=recon)
     part.load_gauge(U)
     psi = to_dev(inputs.gaussian_spinor5d(dims, Ls, 22, nrhs=nrhs))
-    precs = ("f16", "bf16") if tc == "1" else ("f64", "f32", "f16", "bf16")
+    precs = {"1": ("f16", "bf16"), "0": ("f64", "f32", "f16", "bf16", "i16"), "pair": ("f32", "f16", "bf16", "i16")}[tc]
     for prec in precs:
         for op in OPS:
+            if tc == "pair":
+                monkeypatch.setenv("MDWF_FORCE_NS", "4")
             ref = _whole(m, whole, op, prec, psi, nrhs)
+            if tc == "pair":
+                monkeypatch.setenv("MDWF_FORCE_NS", str(PAIR_BIT | 4))
             got = part.apply(op, prec, psi, nrhs)
             assert torch.equal(got, ref), (op, prec, nparts, float((got - ref).abs().max()))
 
