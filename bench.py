@@ -509,7 +509,9 @@ def main():
     ap.add_argument("--workload", default="24^3x64_Ls10", choices=sorted(WORKLOADS) + list(MODES))
     ap.add_argument("--group", type=int, default=3, help="batch32: right-hand sides per multi-RHS launch")
     ap.add_argument("--fp64-solves", type=int, default=16, help="graphbatch: solves repeated with plain FP64")
-    ap.add_argument("--sloppy", default="f16", choices=["f16", "bf16", "f32", "i16"])
+    ap.add_argument("--sloppy", default="f16", choices=["f16", "bf16", "f32", "i16", "f64", "f64e"],
+                    help="inner storage of the mixed solve; with --kernel-only the kernel's precision "
+                         "(f64: FP64, f64e: FP64 storage with emulated-FP64 hops)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--kernel-launches", type=int, default=20)
@@ -637,8 +639,8 @@ def main():
           if k.startswith("hop|") and k.endswith("|p%d|epi2000" % prec) and "|n1|" in k]
     roof_cfg = {"tune_key": rk[0][0], "tune_value": rk[0][1]} if rk else None
     vh = V // 2
-    site = {"f16": 52.0, "bf16": 48.0, "f32": 96.0, "i16": 52.0}[args.sloppy]
-    link = {"f16": 2, "bf16": 2, "f32": 4, "i16": 2}[args.sloppy] * 18.0
+    site = {"f16": 52.0, "bf16": 48.0, "f32": 96.0, "i16": 52.0, "f64": 192.0, "f64e": 192.0}[args.sloppy]
+    link = {"f16": 2, "bf16": 2, "f32": 4, "i16": 2, "f64": 8, "f64e": 8}[args.sloppy] * 18.0
     kbytes = vh * Ls * 2 * site + vh * 8 * link
     peak, peak_kind = peaks()
     achieved = kbytes / (kms * 1e-3) / 1e9
@@ -710,6 +712,7 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "solve": {"mixed_ms": mixed_ms, "iterations": infos[-1].iterations,
                   "reliable_updates": infos[-1].reliable_updates, "fp64_residuals": infos[-1].fp64_residuals,
+                  "emulated_fp64_residuals": infos[-1].emulated_residuals,
                   "true_residual": infos[-1].true_residual,
                   "fp64_ms": fp64["ms"] if fp64 else None, "fp64_iterations": fp64["iterations"] if fp64 else None,
                   "fp64_true_residual": fp64["true_residual"] if fp64 else None,

@@ -68,10 +68,17 @@ enum mdwf_precision {
   MDWF_PREC_F32 = 1,   /* float storage, float arithmetic */
   MDWF_PREC_F16 = 2,   /* half storage + one float norm per 5D site, float arithmetic */
   MDWF_PREC_BF16 = 3,  /* bfloat16 storage, float arithmetic */
-  MDWF_PREC_I16 = 4    /* 16-bit fixed point (the paper's "16-bit fixed-point storage"): per
+  MDWF_PREC_I16 = 4,   /* 16-bit fixed point (the paper's "16-bit fixed-point storage"): per
                           5D site one float norm = max |component| and 24 int16
                           q = RNE(32767 v / norm); links q = RNE(32767 u); float arithmetic
                           (CUDA-core hop only) */
+  MDWF_PREC_F64E = 5   /* mdwf_apply / mdwf_field_bytes / mdwf_pack / mdwf_unpack only: FP64
+                          storage (the MDWF_PREC_F64 layout) with the hops computed in
+                          emulated FP64 -- every real split into a float pair hi + lo, SU(3)
+                          products summed as compensated double-float sums (TwoSum, exact
+                          FMA products), rounded to double once per output real: ~1e-14
+                          relative, on the FP32 pipe; s-direction operators and epilogues in
+                          FP64.  Not on a T-partitioned context (MDWF_ERR_STATE). */
 };
 
 enum mdwf_location { MDWF_HOST = 0, MDWF_DEVICE = 1 };
@@ -125,6 +132,13 @@ typedef struct mdwf_params {
   int t_rank;         /* this context's partition: global timeslices
                          [t_rank * dims[3], (t_rank + 1) * dims[3]); dims[3] is the LOCAL
                          extent (even), the global one is t_ranks * dims[3] */
+  int f64_emulation;  /* nonzero (default): the FP64 hops of a mixed-precision solve --
+                         preparing b~, the reliable-update anchors before the convergence
+                         check, reconstructing x_e -- and of mdwf_make_source_4d run in
+                         emulated FP64 (see MDWF_PREC_F64E); a solve's convergence is always
+                         decided on a residual computed in native FP64, and a plain FP64
+                         solve (sloppy_prec MDWF_PREC_F64) is native FP64 throughout.
+                         Ignored on a T-partitioned context. */
 } mdwf_params;
 
 typedef struct mdwf_solve_params {
@@ -154,12 +168,13 @@ typedef struct mdwf_solve_info {
   double time_ms;          /* wall time of the call (host clock, stream synchronised) */
   int fp64_residuals;      /* residuals b~ - M_pc x recomputed with M_pc in FP64 (the others
                               are updated as res -= M_pc x_s with M_pc in FP32) */
+  int emulated_residuals;  /* of those, how many ran in emulated FP64 (f64_emulation) */
 } mdwf_solve_info;
 
 typedef struct mdwf_ctx mdwf_ctx;
 
 /* Fill *p with defaults: dims 4^4, Ls 8, b5 1.5, c5 0.5, M5 1.3, mf 0.05, t_bc -1,
- * recon 18, check_su3 1, t_ranks 1, t_rank 0. */
+ * recon 18, check_su3 1, t_ranks 1, t_rank 0, f64_emulation 1. */
 void mdwf_default_params(mdwf_params* p);
 /* Defaults: tol 1e-10, maxiter 100000, sloppy F16, delta 0.05, ru_interval 100,
  * check_interval 10, use_graph 1, location DEVICE, full_residual 0, pc_form LEFT. */

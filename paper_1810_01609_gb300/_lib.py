@@ -23,7 +23,7 @@ MDWF_ERR_TIMEOUT = -7
 MDWF_ERR_STATE = -8
 
 MDWF_PREC_F64, MDWF_PREC_F32, MDWF_PREC_F16, MDWF_PREC_BF16, MDWF_PREC_I16 = 0, 1, 2, 3, 4
-PRECS = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "i16": 4}
+PRECS = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3, "i16": 4, "f64e": 5}   # f64e: mdwf_apply only
 MDWF_HOST, MDWF_DEVICE = 0, 1
 MDWF_PC_LEFT, MDWF_PC_SYM = 0, 1
 PC_FORMS = {"left": 0, "sym": 1}
@@ -37,7 +37,7 @@ class mdwf_params(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int * 4), ("Ls", ctypes.c_int), ("b5", ctypes.c_double),
                 ("c5", ctypes.c_double), ("M5", ctypes.c_double), ("mf", ctypes.c_double),
                 ("t_bc", ctypes.c_double), ("gauge_recon", ctypes.c_int), ("check_su3", ctypes.c_int),
-                ("t_ranks", ctypes.c_int), ("t_rank", ctypes.c_int)]
+                ("t_ranks", ctypes.c_int), ("t_rank", ctypes.c_int), ("f64_emulation", ctypes.c_int)]
 
 
 class mdwf_solve_params(ctypes.Structure):
@@ -50,7 +50,8 @@ class mdwf_solve_params(ctypes.Structure):
 class mdwf_solve_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("reliable_updates", ctypes.c_int),
                 ("true_residual", ctypes.c_double), ("full_residual", ctypes.c_double),
-                ("time_ms", ctypes.c_double), ("fp64_residuals", ctypes.c_int)]
+                ("time_ms", ctypes.c_double), ("fp64_residuals", ctypes.c_int),
+                ("emulated_residuals", ctypes.c_int)]
 
 
 class MdwfError(RuntimeError):

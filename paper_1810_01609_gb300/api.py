@@ -7,13 +7,14 @@ from . import _lib as L
 
 class Context:
     def __init__(self, dims, Ls, b5=1.5, c5=0.5, M5=1.3, mf=0.05, t_bc=-1.0, recon=18, check_su3=True,
-                 t_ranks=1, t_rank=0):
+                 t_ranks=1, t_rank=0, f64_emulation=True):
         p = L.mdwf_default_params()
         for i in range(4):
             p.dims[i] = int(dims[i])
         p.Ls, p.b5, p.c5, p.M5, p.mf, p.t_bc = int(Ls), b5, c5, M5, mf, t_bc
         p.gauge_recon, p.check_su3 = int(recon), int(bool(check_su3))
         p.t_ranks, p.t_rank = int(t_ranks), int(t_rank)
+        p.f64_emulation = int(bool(f64_emulation))
         self.params = p
         self.dims = tuple(int(d) for d in dims)
         self.Ls = int(Ls)

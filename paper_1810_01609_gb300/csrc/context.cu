@@ -99,7 +99,20 @@ struct mdwf_ctx {
   void* user_faces[4] = {};          // caller-owned face buffers (send lo/hi, recv lo/hi)
   size_t user_face_bytes = 0;
   std::shared_ptr<void> group;       // in-process partition group this context belongs to
+  // FP64 hops of the calls in progress run in emulated FP64 (double-float; set around the
+  // operator applications that use it, never on a T-partitioned context)
+  bool emu_active = false;
 };
+
+// emulated-FP64 hops for the lifetime of the scope (restores the previous setting)
+struct EmuScope {
+  mdwf_ctx* c;
+  bool old;
+  EmuScope(mdwf_ctx* cc, bool on) : c(cc), old(cc->emu_active) { c->emu_active = on && c->prm.t_ranks == 1; }
+  ~EmuScope() { c->emu_active = old; }
+};
+
+constexpr int PREC_F64E = 5;   // MDWF_PREC_F64E: FP64 storage, emulated-FP64 hops
 
 namespace {
 
@@ -478,7 +491,7 @@ int hop_partitioned(mdwf_ctx* c, int prec, bool dag, bool r12, bool epi, const H
     q.x_begin = x0; q.x_end = x1;
     q.face_mode = mode; q.face = face; q.face_norm = face ? norm_of(face) : nullptr; q.face_base = base;
     cudaError_t err = tc ? launch_hop_tc(prec, dag, r12, epi, q, st)
-                         : launch_hop(prec, dag, r12, epi, (cfg & kOccBit) != 0, (cfg & kPairBit) != 0, q, st);
+                         : launch_hop(prec, dag, r12, epi, (cfg & kOccBit) != 0, (cfg & kPairBit) != 0, false, q, st);
     c->launches++;
     if (err != cudaSuccess) { set_err("launch_hop", err); return MDWF_ERR_CUDA; }
     return MDWF_SUCCESS;
@@ -564,8 +577,9 @@ int hop(mdwf_ctx* c, int prec, bool dag, const Field& in, const Field& out, int 
     const int want = std::min(ns_default(W), cands.back() & 0xFFFF);
     for (int v : cands) if (v == want) dflt = v;
   }
+  const bool emu = prec == F64 && c->emu_active;
   const std::string key = key_of(c, dag ? "hopdag" : "hop", prec, in.nrhs,
-                                 std::string(tc_only ? "tc" : "") + (e.on ? "epi" : "plain") + chain_sig(e.post) +
+                                 std::string(tc_only ? "tc" : "") + (emu ? "emu" : "") + (e.on ? "epi" : "plain") + chain_sig(e.post) +
                                      chain_sig(e.fin) + (p.has_center ? "c" : "") + (p.axpy_r ? "a" : "") +
                                      (red.mode ? "r" : ""));
   p.x_begin = 0;
@@ -597,7 +611,7 @@ int hop(mdwf_ctx* c, int prec, bool dag, const Field& in, const Field& out, int 
       q.red.counter = c->counter;
     }
     cudaError_t err = tc ? launch_hop_tc(prec, dag, r12, e.on, q, st)
-                         : launch_hop(prec, dag, r12, e.on, (cfg & kOccBit) != 0, (cfg & kPairBit) != 0, q, st);
+                         : launch_hop(prec, dag, r12, e.on, (cfg & kOccBit) != 0, (cfg & kPairBit) != 0, emu, q, st);
     c->launches++;
     c->bytes += half_bytes(in, prec) + gauge_bytes(c, prec) + (q.has_center ? half_bytes(e.center, prec) : 0.0) +
                 (q.axpy_r ? 2.0 * half_bytes(e.raxpy, prec) : half_bytes(out, prec));
@@ -980,6 +994,7 @@ struct SolveState {
   std::vector<int> iters;
   int ru = 0;
   int fp64_res = 0;               // FP64 recomputations of b~ - M x
+  int emu_res = 0;                // ... of which in emulated FP64
 };
 
 // res = b~ - M x (FP64), |res|^2 per rhs
@@ -1142,8 +1157,31 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
       }
       if (anchor) {
         if (!folded) CKS(sl_convert(c, F64, x64, F32, v.x, true, true, st));
-        CKS(true_residual(c, form, bt, x64, res, rr2, st));
+        // An anchor that may decide convergence (the inner stop or the incremental
+        // residual says the tolerance is reached) runs in native FP64; the others in
+        // emulated FP64 when the context allows it, and are redone natively should they
+        // find the tolerance reached.
+        bool may_finish = false;
+        for (int r = 0; r < nrhs; r++) {
+          if (S->done[r]) continue;
+          if (c->cg_host[r].hit || (!rr2.empty() && rr2[r] <= sp->tol * sp->tol * S->bnorm2[r])) may_finish = true;
+        }
+        const bool emu = c->prm.f64_emulation && c->prm.t_ranks == 1 && !may_finish;
+        {
+          EmuScope es(c, emu);
+          CKS(true_residual(c, form, bt, x64, res, rr2, st));
+        }
         S->fp64_res++;
+        if (emu) {
+          S->emu_res++;
+          bool reached = false;
+          for (int r = 0; r < nrhs; r++)
+            if (!S->done[r] && rr2[r] <= sp->tol * sp->tol * S->bnorm2[r]) reached = true;
+          if (reached) {
+            CKS(true_residual(c, form, bt, x64, res, rr2, st));
+            S->fp64_res++;
+          }
+        }
         ru_since_anchor = 0;
         x_fresh = true;
         anchor_r2 = rr2;
@@ -1307,6 +1345,7 @@ void mdwf_default_params(mdwf_params* p) {
   p->Ls = 8; p->b5 = 1.5; p->c5 = 0.5; p->M5 = 1.3; p->mf = 0.05; p->t_bc = -1.0;
   p->gauge_recon = 18; p->check_su3 = 1;
   p->t_ranks = 1; p->t_rank = 0;
+  p->f64_emulation = 1;
 }
 
 void mdwf_default_solve_params(mdwf_solve_params* sp) {
@@ -1458,6 +1497,7 @@ int mdwf_load_gauge(mdwf_ctx* c, const double* links, int where, void* stream) {
 }
 
 int mdwf_field_bytes(const mdwf_ctx* c, int prec, int nrhs, size_t* bytes) {
+  if (prec == PREC_F64E) prec = F64;
   if (!c || !bytes || prec < 0 || prec > 4 || nrhs < 1) { g_last_error = "bad argument"; return MDWF_ERR_ARG; }
   *bytes = full_bytes(c, prec, nrhs);
   return MDWF_SUCCESS;
@@ -1469,6 +1509,7 @@ static int check_nrhs(const mdwf_ctx* c, int nrhs) {
 }
 
 int mdwf_pack(mdwf_ctx* c, const double* user5d, void* internal, int prec, int nrhs, void* stream) {
+  if (prec == PREC_F64E) prec = F64;
   if (!c || !user5d || !internal || prec < 0 || prec > 4 || nrhs < 1) { g_last_error = "bad argument"; return MDWF_ERR_ARG; }
   PackParams p;
   p.g = c->g; p.Ls = c->Ls; p.nrhs = nrhs; p.user = user5d; p.user_out = nullptr;
@@ -1483,6 +1524,7 @@ int mdwf_pack(mdwf_ctx* c, const double* user5d, void* internal, int prec, int n
 }
 
 int mdwf_unpack(mdwf_ctx* c, const void* internal, double* user5d, int prec, int nrhs, void* stream) {
+  if (prec == PREC_F64E) prec = F64;
   if (!c || !user5d || !internal || prec < 0 || prec > 4 || nrhs < 1) { g_last_error = "bad argument"; return MDWF_ERR_ARG; }
   PackParams p;
   p.g = c->g; p.Ls = c->Ls; p.nrhs = nrhs; p.user = nullptr; p.user_out = user5d;
@@ -1497,9 +1539,16 @@ int mdwf_unpack(mdwf_ctx* c, const void* internal, double* user5d, int prec, int
 }
 
 int mdwf_apply(mdwf_ctx* c, int op, int prec, const void* in, void* out, int nrhs, void* stream) {
+  const bool emu = prec == PREC_F64E;
+  if (emu) prec = F64;
   if (!c || !in || !out || prec < 0 || prec > 4 || op < 0 || op >= MDWF_OP_COUNT || in == out) {
     g_last_error = "bad argument"; return MDWF_ERR_ARG;
   }
+  if (emu && c->prm.t_ranks > 1) {
+    g_last_error = "emulated FP64 is not available on a T-partitioned context";
+    return MDWF_ERR_STATE;
+  }
+  EmuScope scope(c, emu);
   CKS(check_nrhs(c, nrhs));
   if (!c->gauge_loaded) { g_last_error = "no gauge field loaded"; return MDWF_ERR_STATE; }
   CKS(ensure_small(c));
@@ -1586,8 +1635,13 @@ int mdwf_solve_multi(mdwf_ctx* c, int nrhs, const double* src, double* sol, cons
   CKS(ws_get(c, "x_int", full_bytes(c, F64, nrhs), &xint));
   Field x[2] = {view(c, xint, F64, nrhs, 0), view(c, xint, F64, nrhs, 1)};
   xo = x[1];
+  // the FP64 hops of preparing b~ and reconstructing x_e run in emulated FP64 in a mixed
+  // solve when the context allows it (their ~1e-14 relative rounding is far below the
+  // tolerance, and the convergence check is native FP64)
+  const bool emu = sp->sloppy_prec != F64 && c->prm.f64_emulation && c->prm.t_ranks == 1;
   CKS(sl_chain(c, F64, te, b[0], chain(o.A5inv(false), o.D5(false)), 1.0, nullptr, 0.0, o.mf, st));
   {
+    EmuScope es(c, emu);
     Epi e;
     e.on = true; e.hc = 0.5; e.center = b[1]; e.fin = chain(o.A5inv(false)); e.mf = o.mf;
     CKS(hop(c, F64, false, te, bt, 1, e, red_none(), st));
@@ -1609,6 +1663,7 @@ int mdwf_solve_multi(mdwf_ctx* c, int nrhs, const double* src, double* sol, cons
     CKS(sl_chain(c, F64, te, xo, chain(o.D5(false)), 1.0, nullptr, 0.0, o.mf, st));
   }
   {
+    EmuScope es(c, emu);
     Epi e;
     e.on = true; e.hc = 0.5; e.center = b[0]; e.fin = chain(o.A5inv(false)); e.mf = o.mf;
     CKS(hop(c, F64, false, te, x[0], 0, e, red_none(), st));
@@ -1639,6 +1694,7 @@ int mdwf_solve_multi(mdwf_ctx* c, int nrhs, const double* src, double* sol, cons
     info[r].iterations = S.iters[r];
     info[r].reliable_updates = S.ru;
     info[r].fp64_residuals = S.fp64_res;
+    info[r].emulated_residuals = S.emu_res;
     info[r].true_residual = S.true_rel[r];
     info[r].full_residual = full_rel[r];
     info[r].time_ms = ms;
@@ -1701,7 +1757,10 @@ int mdwf_make_source_4d(mdwf_ctx* c, const double* src4d, double* src5d, int nrh
   CKS(mdwf_pack(c, (const double*)wall, wi, F64, nrhs, st));
   Field fi[2] = {view(c, wi, F64, nrhs, 0), view(c, wi, F64, nrhs, 1)};
   Field fo[2] = {view(c, di, F64, nrhs, 0), view(c, di, F64, nrhs, 1)};
-  CKS(apply_full(c, F64, false, fi, fo, 1.0, st));  // Pauli-Villars D(mf = 1)
+  {
+    EmuScope es(c, c->prm.f64_emulation != 0);   // emulated FP64 where the context allows it
+    CKS(apply_full(c, F64, false, fi, fo, 1.0, st));  // Pauli-Villars D(mf = 1)
+  }
   CKS(mdwf_unpack(c, di, out, F64, nrhs, st));
   return finish_out(src5d, out, b5, where, st);
 }

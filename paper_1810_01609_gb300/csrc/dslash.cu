@@ -9,8 +9,8 @@
 namespace mdwf {
 
 template <int P>
-cudaError_t launch_hop_prec(const HopParams& p, bool dag, bool r12, bool epi, bool occ, int threads, size_t smem,
-                            cudaStream_t st);
+cudaError_t launch_hop_prec(const HopParams& p, bool dag, bool r12, bool epi, bool occ, bool emu, int threads,
+                            size_t smem, cudaStream_t st);
 template <int P>
 cudaError_t launch_hop2_prec(const HopParams& p, bool dag, bool r12, bool epi, int threads, size_t smem,
                              cudaStream_t st);
@@ -34,8 +34,9 @@ size_t hop_smem_bytes(int prec, const HopParams& p, bool epi, bool pair) {
   return pre + epi_smem_bytes(csz, p.ns, p.in.nrhs, p.in.Ls, p.has_center, hop_threads(p, pair));
 }
 
-cudaError_t launch_hop(int prec, bool dag, bool r12, bool epi, bool occ, bool pair, const HopParams& p,
+cudaError_t launch_hop(int prec, bool dag, bool r12, bool epi, bool occ, bool pair, bool emu, const HopParams& p,
                        cudaStream_t st) {
+  if (emu && prec != F64) return cudaErrorInvalidValue;
   const int threads = hop_threads(p, pair);
   const size_t smem = hop_smem_bytes(prec, p, epi, pair);
   if (pair) {
@@ -49,11 +50,11 @@ cudaError_t launch_hop(int prec, bool dag, bool r12, bool epi, bool occ, bool pa
     return cudaErrorInvalidValue;
   }
   switch (prec) {
-    case F64: return launch_hop_prec<F64>(p, dag, r12, epi, occ, threads, smem, st);
-    case F32: return launch_hop_prec<F32>(p, dag, r12, epi, occ, threads, smem, st);
-    case F16: return launch_hop_prec<F16>(p, dag, r12, epi, occ, threads, smem, st);
-    case BF16: return launch_hop_prec<BF16>(p, dag, r12, epi, occ, threads, smem, st);
-    case I16: return launch_hop_prec<I16>(p, dag, r12, epi, occ, threads, smem, st);
+    case F64: return launch_hop_prec<F64>(p, dag, r12, epi, occ, emu, threads, smem, st);
+    case F32: return launch_hop_prec<F32>(p, dag, r12, epi, occ, emu, threads, smem, st);
+    case F16: return launch_hop_prec<F16>(p, dag, r12, epi, occ, emu, threads, smem, st);
+    case BF16: return launch_hop_prec<BF16>(p, dag, r12, epi, occ, emu, threads, smem, st);
+    case I16: return launch_hop_prec<I16>(p, dag, r12, epi, occ, emu, threads, smem, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -2,5 +2,5 @@
 #include "dslash_impl.cuh"
 
 namespace mdwf {
-template cudaError_t launch_hop_prec<F32>(const HopParams&, bool, bool, bool, bool, int, size_t, cudaStream_t);
+template cudaError_t launch_hop_prec<F32>(const HopParams&, bool, bool, bool, bool, bool, int, size_t, cudaStream_t);
 }  // namespace mdwf

@@ -3,5 +3,5 @@
 #include "dslash_impl.cuh"
 
 namespace mdwf {
-template cudaError_t launch_hop_prec<I16>(const HopParams&, bool, bool, bool, bool, int, size_t, cudaStream_t);
+template cudaError_t launch_hop_prec<I16>(const HopParams&, bool, bool, bool, bool, bool, int, size_t, cudaStream_t);
 }  // namespace mdwf

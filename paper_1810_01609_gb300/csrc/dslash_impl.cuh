@@ -17,6 +17,7 @@
 #include "mdwf_impl.cuh"
 #include "mdwf_kernels.h"
 #include "mdwf_epi.cuh"
+#include "mdwf_df.cuh"
 #include <type_traits>
 
 namespace mdwf {
@@ -142,39 +143,44 @@ __device__ __forceinline__ auto mk2(float a, float b) {
   else return __floats2bfloat162_rn(a, b);
 }
 
-// Neighbour column -> projected half spinor h (slot j, colour c at h[6j + 2c]) in the
-// compute precision.  F16 / BF16 project in 16-bit pairs before converting (one rounding
-// of the pair sum, then exact conversion), then scale by the per-site norm.
+// A neighbour column of a 16-bit field as stored: its three 16-byte chunks (one colour's
+// four spins each) and its scale (F16 / int16 norm, 1 for BF16).  Loading and projecting
+// are separate steps so that a hop loop can load the next direction's column while it
+// computes the current one.
+struct Raw16 { uint4 q[3]; float n; };
+
+template <int P>
+__device__ __forceinline__ void raw_load16(const Field& f, unsigned nbr, int col, Raw16& r) {
+  const uint4* d = (const uint4*)f.data;
+  const unsigned W = (unsigned)f.W();
+#pragma unroll
+  for (int c = 0; c < 3; c++) r.q[c] = __ldg(d + (nbr * 3 + c) * W + col);
+  r.n = 1.0f;
+  if constexpr (P == F16 || P == I16) r.n = __ldg(f.norm + nbr * W + col);
+}
+
+// Projected half spinor h (slot j, colour c at h[6j + 2c]) of a raw 16-bit column; returns
+// the scale folded into the accumulation.  F16 / BF16 project in 16-bit pairs (one
+// rounding of the pair sum, then exact conversion); int16 converts its exact integers and
+// projects in FP32, its scale being norm / 32767.
 template <int P, int MU, int SIG>
-__device__ __forceinline__ typename PT<P>::C load_proj(const Field& f, unsigned nbr, int col, typename PT<P>::C h[12]) {
-  using C = typename PT<P>::C;
-  if constexpr (P == F64 || P == F32 || P == I16) {
-    C psi[24];
-    C nrm = (C)1;
-    if constexpr (P == I16) {
-      // exact integers projected in FP32; the site's scale norm / 32767 is returned and
-      // folded into the accumulation like the F16 norm
-      const uint4* d = (const uint4*)f.data;
-      const unsigned W = (unsigned)f.W();
-      nrm = __ldg(f.norm + nbr * W + col) * I16_INV;
+__device__ __forceinline__ float proj16(const Raw16& r, float h[12]) {
+  if constexpr (P == I16) {
+    float psi[24];
 #pragma unroll
-      for (int c = 0; c < 3; c++) {
-        const uint4 q = __ldg(d + (nbr * 3 + c) * W + col);
-        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+    for (int c = 0; c < 3; c++) {
+      const uint32_t w[4] = {r.q[c].x, r.q[c].y, r.q[c].z, r.q[c].w};
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-          const float2 fv = i16x2_to_float2(w[j]);
-          psi[8 * c + 2 * j] = fv.x; psi[8 * c + 2 * j + 1] = fv.y;
-        }
+      for (int j = 0; j < 4; j++) {
+        const float2 fv = i16x2_to_float2(w[j]);
+        psi[8 * c + 2 * j] = fv.x; psi[8 * c + 2 * j + 1] = fv.y;
       }
-    } else {
-      load_site<P>(f, nbr, col, psi);
     }
-    const C sg = (C)SIG;
+    const float sg = (float)SIG;
 #pragma unroll
     for (int co = 0; co < 3; co++) {
-      C* h0 = h + 2 * co;
-      C* h1 = h + 6 + 2 * co;
+      float* h0 = h + 2 * co;
+      float* h1 = h + 6 + 2 * co;
       if (MU == 0) {
         h0[0] = PRE(0, co) + sg * PIM(3, co); h0[1] = PIM(0, co) - sg * PRE(3, co);
         h1[0] = PRE(1, co) + sg * PIM(2, co); h1[1] = PIM(1, co) - sg * PRE(2, co);
@@ -189,17 +195,13 @@ __device__ __forceinline__ typename PT<P>::C load_proj(const Field& f, unsigned 
         h1[0] = PRE(1, co) - sg * PRE(3, co); h1[1] = PIM(1, co) - sg * PIM(3, co);
       }
     }
-    return nrm;
+    return r.n * I16_INV;
   } else {
     using H2 = typename std::conditional<P == F16, __half2, __nv_bfloat162>::type;
-    const uint4* d = (const uint4*)f.data;
-    const unsigned W = (unsigned)f.W();
-    float nrm = 1.0f;
-    if constexpr (P == F16) nrm = __ldg(f.norm + nbr * W + col);
     const H2 ps = mk2<P>((float)SIG, (float)SIG);
 #pragma unroll
     for (int co = 0; co < 3; co++) {
-      const uint4 q = __ldg(d + (nbr * 3 + co) * W + col);
+      const uint4 q = r.q[co];
       const H2 w0 = *(const H2*)&q.x, w1 = *(const H2*)&q.y, w2 = *(const H2*)&q.z, w3 = *(const H2*)&q.w;
       H2 r0, r1;
       if (MU == 0 || MU == 2) {
@@ -223,7 +225,42 @@ __device__ __forceinline__ typename PT<P>::C load_proj(const Field& f, unsigned 
       h[2 * co] = f0.x; h[2 * co + 1] = f0.y;
       h[6 + 2 * co] = f1.x; h[6 + 2 * co + 1] = f1.y;
     }
-    return nrm;
+    return r.n;
+  }
+}
+
+// Neighbour column -> projected half spinor h in the compute precision; returns the scale
+// folded into the accumulation (1 for FP64 / FP32 / BF16).
+template <int P, int MU, int SIG>
+__device__ __forceinline__ typename PT<P>::C load_proj(const Field& f, unsigned nbr, int col, typename PT<P>::C h[12]) {
+  using C = typename PT<P>::C;
+  if constexpr (P == F64 || P == F32) {
+    C psi[24];
+    load_site<P>(f, nbr, col, psi);
+    const C sg = (C)SIG;
+#pragma unroll
+    for (int co = 0; co < 3; co++) {
+      C* h0 = h + 2 * co;
+      C* h1 = h + 6 + 2 * co;
+      if (MU == 0) {
+        h0[0] = PRE(0, co) + sg * PIM(3, co); h0[1] = PIM(0, co) - sg * PRE(3, co);
+        h1[0] = PRE(1, co) + sg * PIM(2, co); h1[1] = PIM(1, co) - sg * PRE(2, co);
+      } else if (MU == 1) {
+        h0[0] = PRE(0, co) - sg * PRE(3, co); h0[1] = PIM(0, co) - sg * PIM(3, co);
+        h1[0] = PRE(1, co) + sg * PRE(2, co); h1[1] = PIM(1, co) + sg * PIM(2, co);
+      } else if (MU == 2) {
+        h0[0] = PRE(0, co) + sg * PIM(2, co); h0[1] = PIM(0, co) - sg * PRE(2, co);
+        h1[0] = PRE(1, co) - sg * PIM(3, co); h1[1] = PIM(1, co) + sg * PRE(3, co);
+      } else {
+        h0[0] = PRE(0, co) - sg * PRE(2, co); h0[1] = PIM(0, co) - sg * PIM(2, co);
+        h1[0] = PRE(1, co) - sg * PRE(3, co); h1[1] = PIM(1, co) - sg * PIM(3, co);
+      }
+    }
+    return (C)1;
+  } else {
+    Raw16 r;
+    raw_load16<P>(f, nbr, col, r);
+    return proj16<P, MU, SIG>(r, h);
   }
 }
 
@@ -244,15 +281,104 @@ __device__ __forceinline__ typename PT<P>::C load_face(const HopParams& p, unsig
   return (C)1;
 }
 
+// ---------------------------------------------------------------- emulated FP64 hop
+// FP64 storage, double-float arithmetic (mdwf_df.cuh): the neighbour's reals and the links
+// are split into float pairs, projected with TwoSum, multiplied and accumulated over all
+// eight directions as compensated sums, and rounded to double once per output real.
+
+// neighbour column -> projected half spinor (slot j, colour c at h[6j + 2c]) in double-float
+template <int MU, int SIG>
+__device__ __forceinline__ void load_proj_emu(const Field& f, unsigned nbr, int col, dfl h[12]) {
+  const double2* d = (const double2*)f.data;
+  const long long W = f.W();
+  constexpr int S = SIG;
+#pragma unroll
+  for (int co = 0; co < 3; co++) {
+    dfl re[4], im[4];
+#pragma unroll
+    for (int sp = 0; sp < 4; sp++) {
+      const double2 q = __ldg(d + ((long long)nbr * 12 + co * 4 + sp) * W + col);
+      re[sp] = split_f64(q.x); im[sp] = split_f64(q.y);
+    }
+    dfl* h0 = h + 2 * co;
+    dfl* h1 = h + 6 + 2 * co;
+    if (MU == 0) {         // h0 = p0 - s i p3 ; h1 = p1 - s i p2
+      h0[0] = dadd<S>(re[0], im[3]); h0[1] = dadd<-S>(im[0], re[3]);
+      h1[0] = dadd<S>(re[1], im[2]); h1[1] = dadd<-S>(im[1], re[2]);
+    } else if (MU == 1) {  // h0 = p0 - s p3 ; h1 = p1 + s p2
+      h0[0] = dadd<-S>(re[0], re[3]); h0[1] = dadd<-S>(im[0], im[3]);
+      h1[0] = dadd<S>(re[1], re[2]); h1[1] = dadd<S>(im[1], im[2]);
+    } else if (MU == 2) {  // h0 = p0 - s i p2 ; h1 = p1 + s i p3
+      h0[0] = dadd<S>(re[0], im[2]); h0[1] = dadd<-S>(im[0], re[2]);
+      h1[0] = dadd<-S>(re[1], im[3]); h1[1] = dadd<S>(im[1], re[3]);
+    } else {               // h0 = p0 - s p2 ; h1 = p1 - s p3
+      h0[0] = dadd<-S>(re[0], re[2]); h0[1] = dadd<-S>(im[0], im[2]);
+      h1[0] = dadd<-S>(re[1], re[3]); h1[1] = dadd<-S>(im[1], im[3]);
+    }
+  }
+}
+
+// a face's projected half spinor (FP64, packed by pack_face_kernel) in double-float
+__device__ __forceinline__ void load_face_emu(const HopParams& p, unsigned nbr, int col, dfl h[12]) {
+  double t[12];
+  load_face<F64>(p, nbr, col, t);
+#pragma unroll
+  for (int k = 0; k < 12; k++) h[k] = split_f64(t[k]);
+}
+
+// SU(3) on h and reconstruction, compensated: u = U h per colour row, then the upper spins
+// += u and the lower ones += -sig X_mu^+ u
+template <int MU, int SIG>
+__device__ __forceinline__ void su3_recon_emu(const dfl h[12], const dfl* U, dacc acc[24]) {
+  constexpr int S = SIG;
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    dacc u0r, u0i, u1r, u1i;
+    {
+      const dfl ur = U[6 * a], ui = U[6 * a + 1];
+      u0r = dprod<1>(ur, h[0]); dfma<-1>(u0r, ui, h[1]);
+      u0i = dprod<1>(ur, h[1]); dfma<1>(u0i, ui, h[0]);
+      u1r = dprod<1>(ur, h[6]); dfma<-1>(u1r, ui, h[7]);
+      u1i = dprod<1>(ur, h[7]); dfma<1>(u1i, ui, h[6]);
+    }
+#pragma unroll
+    for (int b = 1; b < 3; b++) {
+      const dfl ur = U[2 * (3 * a + b)], ui = U[2 * (3 * a + b) + 1];
+      dfma<1>(u0r, ur, h[2 * b]); dfma<-1>(u0r, ui, h[2 * b + 1]);
+      dfma<1>(u0i, ur, h[2 * b + 1]); dfma<1>(u0i, ui, h[2 * b]);
+      dfma<1>(u1r, ur, h[6 + 2 * b]); dfma<-1>(u1r, ui, h[6 + 2 * b + 1]);
+      dfma<1>(u1i, ur, h[6 + 2 * b + 1]); dfma<1>(u1i, ui, h[6 + 2 * b]);
+    }
+    dacc_add<1>(ARE(0, a), u0r); dacc_add<1>(AIM(0, a), u0i);
+    dacc_add<1>(ARE(1, a), u1r); dacc_add<1>(AIM(1, a), u1i);
+    if (MU == 0) {         // lower0 = s i Uh1 ; lower1 = s i Uh0
+      dacc_add<-S>(ARE(2, a), u1i); dacc_add<S>(AIM(2, a), u1r);
+      dacc_add<-S>(ARE(3, a), u0i); dacc_add<S>(AIM(3, a), u0r);
+    } else if (MU == 1) {  // lower0 = s Uh1 ; lower1 = -s Uh0
+      dacc_add<S>(ARE(2, a), u1r); dacc_add<S>(AIM(2, a), u1i);
+      dacc_add<-S>(ARE(3, a), u0r); dacc_add<-S>(AIM(3, a), u0i);
+    } else if (MU == 2) {  // lower0 = s i Uh0 ; lower1 = -s i Uh1
+      dacc_add<-S>(ARE(2, a), u0i); dacc_add<S>(AIM(2, a), u0r);
+      dacc_add<S>(ARE(3, a), u1i); dacc_add<-S>(AIM(3, a), u1r);
+    } else {               // lower0 = -s Uh0 ; lower1 = -s Uh1
+      dacc_add<-S>(ARE(2, a), u0r); dacc_add<-S>(AIM(2, a), u0i);
+      dacc_add<-S>(ARE(3, a), u1r); dacc_add<-S>(AIM(3, a), u1i);
+    }
+  }
+}
+
 // Link staging stride in shared memory (compute-precision reals per link, 16-byte rows)
 template <typename C> __host__ __device__ constexpr int link_stride() { return sizeof(C) == 8 ? 18 : 20; }
 
 // OCC: the occupancy-bounded build (at least 4 CTAs of MAXTHREADS per SM, i.e. at most 64
 // registers, a few spilled); the autotuner picks it or the unbounded one per kernel and
 // lattice (fused 32-bit kernels only)
-template <int P, bool DAG, bool R12, bool EPI, bool OCC>
+// EMU (FP64 storage only): the emulated-FP64 hop loop; phase 0 stages the links as
+// double-float pairs, the epilogue runs in FP64 on the rounded hop result
+template <int P, bool DAG, bool R12, bool EPI, bool OCC, bool EMU = false>
 __global__ void __launch_bounds__(MAXTHREADS, OCC ? 4 : 0)
 hop_kernel(const __grid_constant__ HopParams p) {
+  static_assert(!EMU || P == F64, "emulated FP64: FP64 storage only");
   using C = typename PT<P>::C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Ls = p.in.Ls, nrhs = p.in.nrhs;
@@ -283,25 +409,68 @@ hop_kernel(const __grid_constant__ HopParams p) {
     const bool flip = R12 && mu == 3 && p.t_bc < 0 &&
                       (d < 4 ? c[3] == p.g.T - 1 && p.bc_hi : c[3] == 0 && p.bc_lo);
     load_link<P, R12>(p.gauge, (x * 8 + d) * p.gs, U, flip);
+    if constexpr (EMU) {
+      dfl* dl = (dfl*)(slink + i * LSTR);   // 18 pairs in the 18 doubles' space
 #pragma unroll
-    for (int k = 0; k < 18; k++) slink[i * LSTR + k] = U[k];
+      for (int k = 0; k < 18; k++) dl[k] = split_f64(U[k]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 18; k++) slink[i * LSTR + k] = U[k];
+    }
   }
   __syncthreads();
 
   C acc[24];
 #pragma unroll
   for (int i = 0; i < 24; i++) acc[i] = 0;
-  if (active) {
+  if constexpr (EMU) {
+    if (active) {
+      const unsigned* nb = snbr + site_l * 8;
+      const dfl* lk = (const dfl*)(slink + site_l * 8 * LSTR);
+      dacc da[24];
+#pragma unroll
+      for (int i = 0; i < 24; i++) da[i] = {0.0f, 0.0f};
+      dfl h[12];
+#define HOPE_D(D, MU, SIG)                                                                \
+      { if (((D) == 7 && p.face_mode == 1) || ((D) == 3 && p.face_mode == 2)) load_face_emu(p, nb[D], col, h); \
+        else load_proj_emu<MU, SIG>(p.in, nb[D], col, h);                                  \
+        su3_recon_emu<MU, SIG>(h, lk + (D) * LSTR, da); }
+      HOPE_D(0, 0, SF) HOPE_D(4, 0, -SF) HOPE_D(1, 1, SF) HOPE_D(5, 1, -SF)
+      HOPE_D(2, 2, SF) HOPE_D(6, 2, -SF) HOPE_D(3, 3, SF) HOPE_D(7, 3, -SF)
+#undef HOPE_D
+#pragma unroll
+      for (int i = 0; i < 24; i++) acc[i] = dfl_to_f64(da[i].s, da[i].e);
+    }
+  } else if (active) {
     const unsigned* nb = snbr + site_l * 8;
     const C* lk = slink + site_l * 8 * LSTR;
     C h[12];
+    if constexpr (P == F16 || P == BF16 || P == I16) {
+      // 16-bit storage: the next direction's column is loaded (registers ra / rb in turn)
+      // while the current one is projected and multiplied; face directions of a partition
+      // boundary come from the received faces instead
+      Raw16 ra, rb;
+      const bool f3 = p.face_mode == 2, f7 = p.face_mode == 1;
+      raw_load16<P>(p.in, nb[0], col, ra);
+#define HOP_PF(D, MU, SIG, DN, CUR, NXT, FN)                                                  \
+      { if ((DN) >= 0 && !(FN)) raw_load16<P>(p.in, nb[(DN) < 0 ? 0 : (DN)], col, NXT);      \
+        const C nrm = ((D) == 7 && f7) || ((D) == 3 && f3) ? load_face<P>(p, nb[D], col, h)    \
+                                                          : proj16<P, MU, SIG>(CUR, h);        \
+        su3_recon<MU, SIG>(h, lk + (D) * LSTR, acc, nrm); }
+      HOP_PF(0, 0, SF, 4, ra, rb, false) HOP_PF(4, 0, -SF, 1, rb, ra, false)
+      HOP_PF(1, 1, SF, 5, ra, rb, false) HOP_PF(5, 1, -SF, 2, rb, ra, false)
+      HOP_PF(2, 2, SF, 6, ra, rb, false) HOP_PF(6, 2, -SF, 3, rb, ra, f3)
+      HOP_PF(3, 3, SF, 7, ra, rb, f7) HOP_PF(7, 3, -SF, -1, rb, ra, false)
+#undef HOP_PF
+    } else {
 #define HOP_D(D, MU, SIG)                                                                 \
-    { const C nrm = ((D) == 7 && p.face_mode == 1) || ((D) == 3 && p.face_mode == 2)         \
-                        ? load_face<P>(p, nb[D], col, h) : load_proj<P, MU, SIG>(p.in, nb[D], col, h); \
-      su3_recon<MU, SIG>(h, lk + (D) * LSTR, acc, nrm); }
-    HOP_D(0, 0, SF) HOP_D(4, 0, -SF) HOP_D(1, 1, SF) HOP_D(5, 1, -SF)
-    HOP_D(2, 2, SF) HOP_D(6, 2, -SF) HOP_D(3, 3, SF) HOP_D(7, 3, -SF)
+      { const C nrm = ((D) == 7 && p.face_mode == 1) || ((D) == 3 && p.face_mode == 2)       \
+                          ? load_face<P>(p, nb[D], col, h) : load_proj<P, MU, SIG>(p.in, nb[D], col, h); \
+        su3_recon<MU, SIG>(h, lk + (D) * LSTR, acc, nrm); }
+      HOP_D(0, 0, SF) HOP_D(4, 0, -SF) HOP_D(1, 1, SF) HOP_D(5, 1, -SF)
+      HOP_D(2, 2, SF) HOP_D(6, 2, -SF) HOP_D(3, 3, SF) HOP_D(7, 3, -SF)
 #undef HOP_D
+    }
   }
 
   if constexpr (!EPI) {
@@ -453,11 +622,11 @@ cudaError_t launch_hop2_prec(const HopParams& p, bool dag, bool r12, bool epi, i
   return epi ? launch_pair<P, false, false, true>(p, threads, smem, st) : launch_pair<P, false, false, false>(p, threads, smem, st);
 }
 
-template <int P, bool DAG, bool R12, bool EPI, bool OCC = false>
+template <int P, bool DAG, bool R12, bool EPI, bool OCC = false, bool EMU = false>
 static cudaError_t launch_one(const HopParams& p, int threads, size_t smem, cudaStream_t st) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(hop_kernel<P, DAG, R12, EPI, OCC>,
+    cudaError_t e = cudaFuncSetAttribute(hop_kernel<P, DAG, R12, EPI, OCC, EMU>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     attr_set = true;
@@ -465,8 +634,15 @@ static cudaError_t launch_one(const HopParams& p, int threads, size_t smem, cuda
   const long long blocks = (p.x_end - p.x_begin + p.ns - 1) / p.ns;
   HopParams q = p;   // scalars rounded once for the 32-bit kernels
   q.hcf = (float)p.hc; q.ccf = (float)p.cc; q.mff = (float)p.mf;
-  hop_kernel<P, DAG, R12, EPI, OCC><<<(unsigned)blocks, threads, smem, st>>>(q);
+  hop_kernel<P, DAG, R12, EPI, OCC, EMU><<<(unsigned)blocks, threads, smem, st>>>(q);
   return cudaGetLastError();
+}
+
+// the emulated-FP64 variants (FP64 storage)
+template <bool DAG, bool R12>
+static cudaError_t launch_emu(const HopParams& p, bool epi, int threads, size_t smem, cudaStream_t st) {
+  return epi ? launch_one<F64, DAG, R12, true, false, true>(p, threads, smem, st)
+             : launch_one<F64, DAG, R12, false, false, true>(p, threads, smem, st);
 }
 
 template <int P, bool DAG, bool R12>
@@ -477,10 +653,17 @@ static cudaError_t launch_epi(const HopParams& p, bool occ, int threads, size_t 
   return launch_one<P, DAG, R12, true>(p, threads, smem, st);
 }
 
-// all (dagger, 12-real links, epilogue, occupancy-bounded) variants of one storage precision
+// all (dagger, 12-real links, epilogue, occupancy-bounded; FP64: emulated) variants of one
+// storage precision
 template <int P>
-cudaError_t launch_hop_prec(const HopParams& p, bool dag, bool r12, bool epi, bool occ, int threads, size_t smem,
-                            cudaStream_t st) {
+cudaError_t launch_hop_prec(const HopParams& p, bool dag, bool r12, bool epi, bool occ, bool emu, int threads,
+                            size_t smem, cudaStream_t st) {
+  if constexpr (P == F64) {
+    if (emu) {
+      if (dag) return r12 ? launch_emu<true, true>(p, epi, threads, smem, st) : launch_emu<true, false>(p, epi, threads, smem, st);
+      return r12 ? launch_emu<false, true>(p, epi, threads, smem, st) : launch_emu<false, false>(p, epi, threads, smem, st);
+    }
+  }
   if (dag) {
     if (r12) return epi ? launch_epi<P, true, true>(p, occ, threads, smem, st) : launch_one<P, true, true, false>(p, threads, smem, st);
     return epi ? launch_epi<P, true, false>(p, occ, threads, smem, st) : launch_one<P, true, false, false>(p, threads, smem, st);

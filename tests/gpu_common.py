@@ -35,8 +35,12 @@ def rel(a, b):
 # term gives O(1) at the sites it touches.  16-bit fixed point (I16): half a unit of
 # 1/32767 of the site norm on every stored input, link and output (1.5e-5 each) and FP32
 # arithmetic give a few 1e-5; 1e-4 leaves 3x, and the site bound is 2.5x that.
-TOL = {"f64": 1e-13, "f32": 1e-6, "f16": 2e-3, "bf16": 8e-3, "i16": 1e-4}
-SITE_TOL = {"f64": 1e-13, "f32": 1e-6, "f16": 5e-3, "bf16": 2e-2, "i16": 2.5e-4}
+# Emulated FP64 (f64e: float pairs, compensated sums): inputs and links split with a
+# relative error below 2^-46 (1.4e-14), each product exact up to its cross terms (2^-48),
+# each output real a sum of 8 direction terms whose error parts are added in float (a few
+# 2^-48 of the terms): ~1e-14 relative; the FP64 bar 1e-13 leaves several times that.
+TOL = {"f64": 1e-13, "f32": 1e-6, "f16": 2e-3, "bf16": 8e-3, "i16": 1e-4, "f64e": 1e-13}
+SITE_TOL = {"f64": 1e-13, "f32": 1e-6, "f16": 5e-3, "bf16": 2e-2, "i16": 2.5e-4, "f64e": 1e-13}
 
 
 def site_rel(got, ref, keep=None):

@@ -1,7 +1,8 @@
 """GPU parity of the operator kernels (C ABI mdwf_apply / mdwf_pack / mdwf_unpack) against
 the FP64 oracle on the same seeded inputs.  Tolerances: relative 2-norm difference of the
 whole output, FP64 1e-13, FP32 1e-6, F16 (+norm) 2e-3, BF16 8e-3 (8 significant bits:
-unit roundoff 2^-9 on input and output, plus the 16-bit projection and link rounding)."""
+unit roundoff 2^-9 on input and output, plus the 16-bit projection and link rounding),
+emulated FP64 (FP64 storage, double-float hops) 1e-13."""
 import numpy as np
 import pytest
 
@@ -92,7 +93,7 @@ ALL_OPS = ["HOP_EO", "HOP_OE", "HOP_EO_DAG", "HOP_OE_DAG", "D5", "D5_DAG", "M5",
 
 
 @pytest.mark.parametrize("case", CASES)
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16", "i16"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16", "i16", "f64e"])
 def test_apply_parity(case, prec, monkeypatch):
     dims, Ls, nrhs = case
     if dims == (6, 2, 2, 6):

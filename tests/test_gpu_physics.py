@@ -12,13 +12,15 @@ from gpu_common import lib, rel, to_dev, to_host, torch
 pytestmark = pytest.mark.gpu
 
 
-def test_source_projection_fh():
+@pytest.mark.parametrize("emulation", [True, False])
+def test_source_projection_fh(emulation):
+    """emulation: the injection's FP64 hops in emulated FP64 (the default) or native."""
     m = lib()
     dims, Ls, mf = (4, 4, 2, 6), 6, 0.05
     U = inputs.gauge_links(dims, 0.3, 9)
     Ub = dirac.boundary_links(U, -1.0)
     p = MobiusParams(Ls=Ls, mf=mf)
-    ctx = m.Context(dims, Ls, mf=mf)
+    ctx = m.Context(dims, Ls, mf=mf, f64_emulation=emulation)
     ctx.load_gauge(U)
     rng = np.random.default_rng(3)
     b4 = rng.standard_normal((2,) + ctx.shape4d() + (2,)).view(np.complex128)[..., 0]

@@ -164,6 +164,30 @@ def test_incremental_residual_tracks_fp64():
         assert abs(incr - fp64) <= 1e-2 * fp64, (incr, fp64)
 
 
+def test_emulated_fp64_anchors():
+    """f64_emulation (the default): in a mixed solve, b~, x_e and the reliable-update
+    anchors that cannot end the solve use emulated-FP64 hops; convergence is decided on a
+    native FP64 residual.  8^3 x 16, light quark (a mid-solve anchor is due): both settings
+    reach 1e-10 and give the same solution to the accuracy the tolerance allows."""
+    m = lib()
+    dims, Ls = (8, 8, 8, 16), 12
+    U = inputs.gauge_links(dims, 0.5, 7)
+    b = to_dev(inputs.gaussian_spinor5d(dims, Ls, 8))
+    out = {}
+    for emu in (True, False):
+        ctx = m.Context(dims, Ls, mf=0.01, f64_emulation=emu)
+        ctx.load_gauge(U)
+        x, info = ctx.solve(b, sloppy="f16", tol=1e-10, full_residual=True)
+        assert info.status == 0 and info.true_residual <= 1e-10, (emu, info.true_residual)
+        assert info.full_residual <= 1e-9
+        if emu:
+            assert 1 <= info.emulated_residuals < info.fp64_residuals, (info.emulated_residuals, info.fp64_residuals)
+        else:
+            assert info.emulated_residuals == 0
+        out[emu] = to_host(x)
+    assert rel(out[True], out[False]) <= 1e-7
+
+
 @pytest.mark.parametrize("sloppy", ["f64", "f16", "bf16"])
 def test_solve_symmetric_form(sloppy):
     """pc_form = sym: CG on M_sym y = D5 b~_o, x_o = D5^-1 y.  The full solution is the
