@@ -1030,7 +1030,7 @@ int cg_solve(mdwf_ctx* c, const Field& bt, const Field& x64, const mdwf_solve_pa
   CKS(make_cgset(c, P, mixed ? F32 : F64, nrhs, form, &v));
   Field res, r64;
   CKS(ws_half(c, "res64", F64, nrhs, &res));
-  CKS(ws_half(c, "r64", F64, nrhs, &r64));
+  if (!mixed) CKS(ws_half(c, "r64", F64, nrhs, &r64));   // the plain FP64 CG's normal residual
   CK(cudaMemsetAsync(x64.data, 0, field_bytes_of(x64, F64), st));
   CK(cudaMemsetAsync(v.x.data, 0, field_bytes_of(v.x, v.prec_x), st));
   if (v.x.norm) CK(cudaMemsetAsync(v.x.norm, 0, (size_t)c->vh * nrhs * c->Ls * 4, st));
@@ -1745,16 +1745,18 @@ int mdwf_make_source_4d(mdwf_ctx* c, const double* src4d, double* src5d, int nrh
   double* out;
   CKS(stage_in(c, "src4_in", src4d, b4, where, st, &in));
   CKS(stage_out(c, "src5_out", src5d, b5, where, &out));
-  void* wall;
-  CKS(ws_get(c, "src_wall", b5, &wall));
+  // the wall source is built in the output buffer, packed, and the result unpacked over it;
+  // the packed fields share the solver's FP64 source / solution workspaces (a context runs
+  // one call at a time), so injecting costs no memory beyond what a solve of the same nrhs
+  // holds anyway
   SrcParams sp;
-  sp.g = c->g; sp.Ls = c->Ls; sp.nrhs = nrhs; sp.in = in; sp.out = (double*)wall;
+  sp.g = c->g; sp.Ls = c->Ls; sp.nrhs = nrhs; sp.in = in; sp.out = out;
   CK(launch_embed_wall(sp, st));
   c->launches++;
   void *wi, *di;
-  CKS(ws_get(c, "src_wi", full_bytes(c, F64, nrhs), &wi));
-  CKS(ws_get(c, "src_di", full_bytes(c, F64, nrhs), &di));
-  CKS(mdwf_pack(c, (const double*)wall, wi, F64, nrhs, st));
+  CKS(ws_get(c, "b_int", full_bytes(c, F64, nrhs), &wi));
+  CKS(ws_get(c, "x_int", full_bytes(c, F64, nrhs), &di));
+  CKS(mdwf_pack(c, out, wi, F64, nrhs, st));
   Field fi[2] = {view(c, wi, F64, nrhs, 0), view(c, wi, F64, nrhs, 1)};
   Field fo[2] = {view(c, di, F64, nrhs, 0), view(c, di, F64, nrhs, 1)};
   {

@@ -445,32 +445,13 @@ hop_kernel(const __grid_constant__ HopParams p) {
     const unsigned* nb = snbr + site_l * 8;
     const C* lk = slink + site_l * 8 * LSTR;
     C h[12];
-    if constexpr (P == F16 || P == BF16 || P == I16) {
-      // 16-bit storage: the next direction's column is loaded (registers ra / rb in turn)
-      // while the current one is projected and multiplied; face directions of a partition
-      // boundary come from the received faces instead
-      Raw16 ra, rb;
-      const bool f3 = p.face_mode == 2, f7 = p.face_mode == 1;
-      raw_load16<P>(p.in, nb[0], col, ra);
-#define HOP_PF(D, MU, SIG, DN, CUR, NXT, FN)                                                  \
-      { if ((DN) >= 0 && !(FN)) raw_load16<P>(p.in, nb[(DN) < 0 ? 0 : (DN)], col, NXT);      \
-        const C nrm = ((D) == 7 && f7) || ((D) == 3 && f3) ? load_face<P>(p, nb[D], col, h)    \
-                                                          : proj16<P, MU, SIG>(CUR, h);        \
-        su3_recon<MU, SIG>(h, lk + (D) * LSTR, acc, nrm); }
-      HOP_PF(0, 0, SF, 4, ra, rb, false) HOP_PF(4, 0, -SF, 1, rb, ra, false)
-      HOP_PF(1, 1, SF, 5, ra, rb, false) HOP_PF(5, 1, -SF, 2, rb, ra, false)
-      HOP_PF(2, 2, SF, 6, ra, rb, false) HOP_PF(6, 2, -SF, 3, rb, ra, f3)
-      HOP_PF(3, 3, SF, 7, ra, rb, f7) HOP_PF(7, 3, -SF, -1, rb, ra, false)
-#undef HOP_PF
-    } else {
 #define HOP_D(D, MU, SIG)                                                                 \
-      { const C nrm = ((D) == 7 && p.face_mode == 1) || ((D) == 3 && p.face_mode == 2)       \
-                          ? load_face<P>(p, nb[D], col, h) : load_proj<P, MU, SIG>(p.in, nb[D], col, h); \
-        su3_recon<MU, SIG>(h, lk + (D) * LSTR, acc, nrm); }
-      HOP_D(0, 0, SF) HOP_D(4, 0, -SF) HOP_D(1, 1, SF) HOP_D(5, 1, -SF)
-      HOP_D(2, 2, SF) HOP_D(6, 2, -SF) HOP_D(3, 3, SF) HOP_D(7, 3, -SF)
+    { const C nrm = ((D) == 7 && p.face_mode == 1) || ((D) == 3 && p.face_mode == 2)       \
+                        ? load_face<P>(p, nb[D], col, h) : load_proj<P, MU, SIG>(p.in, nb[D], col, h); \
+      su3_recon<MU, SIG>(h, lk + (D) * LSTR, acc, nrm); }
+    HOP_D(0, 0, SF) HOP_D(4, 0, -SF) HOP_D(1, 1, SF) HOP_D(5, 1, -SF)
+    HOP_D(2, 2, SF) HOP_D(6, 2, -SF) HOP_D(3, 3, SF) HOP_D(7, 3, -SF)
 #undef HOP_D
-    }
   }
 
   if constexpr (!EPI) {
