@@ -646,22 +646,17 @@ def main():
     achieved = kbytes / (kms * 1e-3) / 1e9
     del flush
 
-    # end to end through the library's host-buffer path: every call gets pinned HOST
-    # pointers and copies in and out itself (4D source in, 4D propagator column out)
-    sh5 = (1,) + ctx.shape5d()
+    # end to end through the public API with HOST buffers: mdwf_propagator takes the pinned
+    # 4D source, copies it in, injects, solves and projects on the device and copies the
+    # 4D propagator column back (the 5D source and solution never leave the device)
     b4h = b4.cpu().pin_memory()
-    eta_h = torch.empty(sh5, dtype=torch.complex128).pin_memory()
-    x_h = torch.empty(sh5, dtype=torch.complex128).pin_memory()
     q_h = torch.empty((1,) + ctx.shape4d(), dtype=torch.complex128).pin_memory()
-    sp_host = ctx.solve_params(tol=1e-10, sloppy=args.sloppy, location=m.MDWF_HOST)
+    sp_e2e = ctx.solve_params(tol=1e-10, sloppy=args.sloppy)
 
     def step_host():
-        m.mdwf_make_source_4d(ctx.h, b4h, eta_h, 1, stream)
-        info = m.mdwf_solve(ctx.h, eta_h, x_h, sp_host, stream)
-        m.mdwf_project_4d(ctx.h, x_h, q_h, 1, stream)
-        return info
+        return m.mdwf_propagator(ctx.h, 1, b4h, q_h, sp_e2e, stream)[0]
 
-    step_host()   # host-side staging buffers of the context are allocated here
+    step_host()   # the context's host-path staging buffers are allocated here
     torch.cuda.synchronize()
     ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2e_bytes0 = ctx.algorithmic_bytes()
@@ -672,21 +667,20 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = ee0.elapsed_time(ee1) / args.steps
     e2e_val = world * (ctx.algorithmic_bytes() - e2e_bytes0) / args.steps / (e2e_ms * 1e-3) / 1e9
-    b4b, b5b = b4h.numel() * 16, eta_h.numel() * 16
-    # the same pinned 5D buffer copied by torch alone, both ways: the link's own speed
-    dtmp = torch.empty(sh5, dtype=torch.complex128, device="cuda")
+    b4b = b4h.numel() * 16
+    # the same pinned 4D buffer copied by torch alone, both ways: the link's own speed
+    dtmp = torch.empty_like(q_h, device="cuda")
     c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     c0.record(stream)
-    dtmp.copy_(eta_h, non_blocking=True)
+    dtmp.copy_(q_h, non_blocking=True)
     c1.record(stream)
-    eta_h.copy_(dtmp, non_blocking=True)
+    q_h.copy_(dtmp, non_blocking=True)
     c2.record(stream)
     torch.cuda.synchronize()
-    pinned_gbs = {"h2d": b5b / (c0.elapsed_time(c1) * 1e-3) / 1e9, "d2h": b5b / (c1.elapsed_time(c2) * 1e-3) / 1e9}
+    pinned_gbs = {"h2d": b4b / (c0.elapsed_time(c1) * 1e-3) / 1e9, "d2h": b4b / (c1.elapsed_time(c2) * 1e-3) / 1e9}
     del dtmp
-    e2e_h2d = b4b + 2 * b5b      # source (make_source_4d), 5D source (solve), 5D solution (project_4d)
-    e2e_d2h = 2 * b5b + b4b      # 5D source, 5D solution, 4D propagator column
-    del eta_h, x_h
+    e2e_h2d = b4b      # the 4D source
+    e2e_d2h = b4b      # the 4D propagator column
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -725,7 +719,7 @@ def main():
                      "bytes_per_launch": kbytes, "ms_per_launch": kms, "launch_config": roof_cfg},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "GB/s", "ms_per_step": e2e_ms,
-                "path": "mdwf_make_source_4d / mdwf_solve / mdwf_project_4d with pinned HOST pointers",
+                "path": "mdwf_propagator (injection, solve, projection in one C-ABI call) with pinned HOST 4D source and propagator",
                 "true_residual": ih.true_residual,
                 "h2d_bytes_per_step": int(e2e_h2d), "d2h_bytes_per_step": int(e2e_d2h),
                 "pinned_copy_gbs_torch": pinned_gbs},

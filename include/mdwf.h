@@ -237,6 +237,16 @@ int mdwf_make_source_4d(mdwf_ctx* ctx, const double* src4d, double* src5d, int n
 /* 5D solution -> 4D propagator column q = P_- y_0 + P_+ y_{Ls-1}. */
 int mdwf_project_4d(mdwf_ctx* ctx, const double* sol5d, double* q4d, int nrhs, int where,
                     void* stream);
+/* Propagator columns in one call (Sec. "Performance Measurement Method": the propagator
+ * solve from a 4D source): q = P_- y_0 + P_+ y_{Ls-1} with D y = D(mf=1) P (b at s=0),
+ * i.e. mdwf_make_source_4d, mdwf_solve_multi and mdwf_project_4d chained on the device.
+ * src4d and q4d are [nrhs][t][z][y][x][4][3] complex128 at `where` (MDWF_HOST or
+ * MDWF_DEVICE); the 5D source and solution stay in one device workspace of the context
+ * (nrhs * Ls * 4D-field bytes), so a host caller moves only the 4D fields.  sp is used as
+ * for mdwf_solve_multi except sp->location (ignored).  info points to nrhs entries.
+ * Returns the solve's worst status (MDWF_ERR_NOT_CONVERGED: q still written) or an error. */
+int mdwf_propagator(mdwf_ctx* ctx, int nrhs, const double* src4d, double* q4d, int where,
+                    const mdwf_solve_params* sp, mdwf_solve_info* info, void* stream);
 /* Feynman-Hellmann sequential source (Sec. "Current State of the Art": all temporal
  * distances for the cost of one): out(z) = gamma_3 gamma_5 q(z) at every site z of every
  * timeslice, for nrhs 4D columns. */

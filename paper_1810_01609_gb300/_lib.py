@@ -78,6 +78,8 @@ _SIGS = {
     "mdwf_solve_multi": (_I, [_V, _I, _V, _V, ctypes.POINTER(mdwf_solve_params),
                               ctypes.POINTER(mdwf_solve_info), _V]),
     "mdwf_make_source_4d": (_I, [_V, _V, _V, _I, _I, _V]),
+    "mdwf_propagator": (_I, [_V, _I, _V, _V, _I, ctypes.POINTER(mdwf_solve_params),
+                             ctypes.POINTER(mdwf_solve_info), _V]),
     "mdwf_project_4d": (_I, [_V, _V, _V, _I, _I, _V]),
     "mdwf_fh_source": (_I, [_V, _V, _V, _I, _I, _V]),
     "mdwf_contract_nucleon": (_I, [_V, _V, _V, _V, _V, _I, _V]),
@@ -209,6 +211,19 @@ def _io4(fn, ctx, a, b, nrhs, stream):
     if wa != wb:
         raise ValueError("input and output must both be host or both be device arrays")
     return _check(fn(ctx, pa, pb, nrhs, wa, _stream(stream)))
+
+
+def mdwf_propagator(ctx, nrhs, src4d, q4d, sp, stream=None):
+    """4D sources -> 4D propagator columns in one call (host or device arrays, both alike)."""
+    pa, wa = ptr(src4d)
+    pb, wb = ptr(q4d)
+    if wa != wb:
+        raise ValueError("source and propagator must both be host or both be device arrays")
+    infos = (mdwf_solve_info * nrhs)()
+    code = load().mdwf_propagator(ctx, nrhs, pa, pb, wa, ctypes.byref(sp), infos, _stream(stream))
+    if code not in (MDWF_SUCCESS, MDWF_ERR_NOT_CONVERGED):
+        _check(code)
+    return list(infos)
 
 
 def mdwf_make_source_4d(ctx, src4d, src5d, nrhs, stream=None):

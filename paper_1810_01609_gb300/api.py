@@ -84,6 +84,19 @@ class Context:
         infos = L.mdwf_solve_multi(self.h, nrhs, b, sol, sp, stream)
         return sol, infos
 
+    def propagator(self, b4, nrhs=1, q=None, stream=None, **kw):
+        """4D sources [nrhs][t][z][y][x][4][3] -> 4D propagator columns (numpy: host path,
+        torch cuda: device path); returns (q, infos)."""
+        if isinstance(b4, np.ndarray):
+            b4 = np.ascontiguousarray(b4, dtype=np.complex128)
+            q = np.empty_like(b4) if q is None else q
+        else:
+            import torch
+            q = torch.empty_like(b4) if q is None else q
+        sp = self.solve_params(**kw)
+        infos = L.mdwf_propagator(self.h, nrhs, b4, q, sp, stream)
+        return q, infos
+
     def make_source_4d(self, b4, nrhs=1, stream=None):
         out = np.empty((nrhs,) + self.shape5d(), dtype=np.complex128) if isinstance(b4, np.ndarray) else None
         if out is None:

@@ -1783,6 +1783,35 @@ int mdwf_project_4d(mdwf_ctx* c, const double* sol5d, double* q4d, int nrhs, int
   return finish_out(q4d, out, b4, where, st);
 }
 
+// 4D sources -> 4D propagator columns: injection, batched solve and projection chained on
+// the device through one 5D workspace (the solve has packed its source before it writes
+// its solution, so the two share it); only the 4D fields cross to the host.
+int mdwf_propagator(mdwf_ctx* c, int nrhs, const double* src4d, double* q4d, int where,
+                    const mdwf_solve_params* sp, mdwf_solve_info* info, void* stream) {
+  if (!c || !src4d || !q4d || !sp || !info || (where != MDWF_HOST && where != MDWF_DEVICE)) {
+    g_last_error = "bad argument"; return MDWF_ERR_ARG;
+  }
+  CKS(check_nrhs(c, nrhs));
+  if (!c->gauge_loaded) { g_last_error = "no gauge field loaded"; return MDWF_ERR_STATE; }
+  CKS(ensure_small(c));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t b4 = (size_t)nrhs * 2 * c->vh * 12 * 16, b5 = b4 * c->Ls;
+  const double* in;
+  double* out;
+  CKS(stage_in(c, "prop_src4", src4d, b4, where, st, &in));
+  CKS(stage_out(c, "prop_q4", q4d, b4, where, &out));
+  void* f5;
+  CKS(ws_get(c, "prop_5d", b5, &f5));
+  CKS(mdwf_make_source_4d(c, in, (double*)f5, nrhs, MDWF_DEVICE, stream));
+  mdwf_solve_params dsp = *sp;
+  dsp.location = MDWF_DEVICE;
+  const int rs = mdwf_solve_multi(c, nrhs, (const double*)f5, (double*)f5, &dsp, info, stream);
+  if (rs != MDWF_SUCCESS && rs != MDWF_ERR_NOT_CONVERGED) return rs;
+  CKS(mdwf_project_4d(c, (const double*)f5, out, nrhs, MDWF_DEVICE, stream));
+  CKS(finish_out(q4d, out, b4, where, st));
+  return rs;
+}
+
 int mdwf_fh_source(mdwf_ctx* c, const double* q4d, double* out4d, int nrhs, int where, void* stream) {
   if (!c || !q4d || !out4d || nrhs < 1 || (where != MDWF_HOST && where != MDWF_DEVICE)) { g_last_error = "bad argument"; return MDWF_ERR_ARG; }
   CKS(ensure_small(c));

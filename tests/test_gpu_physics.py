@@ -36,6 +36,33 @@ def test_source_projection_fh(emulation):
         assert rel(f[r], hadron.fh_source(q[r])) <= 1e-15
 
 
+def test_propagator_call_matches_chain(monkeypatch):
+    """mdwf_propagator (injection, batched solve and projection chained on the device, one
+    C-ABI call) gives bit for bit the columns of the three separate calls, on the host and
+    on the device path, and the oracle's propagator to the solve's accuracy."""
+    monkeypatch.setenv("MDWF_TC", "0")
+    m = lib()
+    dims, Ls, mf = (4, 4, 2, 6), 6, 0.05
+    U = inputs.gauge_links(dims, 0.3, 9)
+    Ub = dirac.boundary_links(U, -1.0)
+    p = MobiusParams(Ls=Ls, mf=mf)
+    ctx = m.Context(dims, Ls, mf=mf)
+    ctx.load_gauge(U)
+    b4 = np.stack([inputs.point_source4d(dims, 0, 0), inputs.point_source4d(dims, 3, 2)])
+    eta = ctx.make_source_4d(to_dev(b4), nrhs=2)
+    y, infos_c = ctx.solve_multi(eta, tol=1e-10, sloppy="f16")
+    q_chain = to_host(ctx.project_4d(y, nrhs=2))
+    q_dev, infos = ctx.propagator(to_dev(b4), nrhs=2, tol=1e-10, sloppy="f16")
+    q_host, infos_h = ctx.propagator(b4, nrhs=2, tol=1e-10, sloppy="f16")
+    assert all(i.status == 0 and i.true_residual <= 1e-10 for i in infos + infos_h)
+    assert [i.iterations for i in infos] == [i.iterations for i in infos_c]
+    assert np.array_equal(to_host(q_dev), q_chain)
+    assert np.array_equal(q_host, q_chain)
+    for r in range(2):
+        yo, _, _ = solve.solve_eo(Ub, hadron.inject_source(Ub, b4[r], p), p, tol=1e-12)
+        assert rel(q_host[r], hadron.project_4d(yo)) <= 1e-8
+
+
 def _cols_to_oracle(S):
     """[12][t,z,y,x,spin,colour] columns -> oracle layout [t,z,y,x,spin,colour,spin',colour']."""
     T, Z, Y, X = S.shape[1:5]
