@@ -48,6 +48,7 @@ METRIC = "MDWF Dslash HBM GB/s (% of peak); solve time to 1e-10, mixed vs FP64"
 # the files that define the device code and launch of the hop kernels (the roofline kernel)
 KERNEL_FILES = ["dslash.cu", "dslash_bf16.cu", "dslash_f16.cu", "dslash_f32.cu", "dslash_f64.cu", "dslash_i16.cu",
                 "dslash2_bf16.cu", "dslash2_f16.cu", "dslash2_f32.cu", "dslash2_i16.cu",
+                "dslash3_bf16.cu", "dslash3_f16.cu", "dslash3_i16.cu",
                 "dslash_impl.cuh", "dslash_umma.cu", "mdwf_epi.cuh", "mdwf_impl.cuh", "mdwf_kernels.h"]
 
 
@@ -634,7 +635,8 @@ def main():
         kt.append(a.elapsed_time(b))
     kms = float(np.mean(kt))
     # the configuration the autotuner chose for this kernel (sites per CTA; flags 65536:
-    # 64-register build, 131072: tensor-core kernel, 262144: paired-column kernel)
+    # 64-register build, 131072: tensor-core kernel, 262144: paired-column kernel, 524288:
+    # bulk-staged kernel)
     rk = [(k, v) for k, v, _ in ctx.tune_entries()
           if k.startswith("hop|") and k.endswith("|p%d|epi2000" % prec) and "|n1|" in k]
     roof_cfg = {"tune_key": rk[0][0], "tune_value": rk[0][1]} if rk else None

@@ -294,12 +294,13 @@ void load_tune(mdwf_ctx* c) {
     char* end = nullptr;
     e.ns = (int)strtol(line.c_str() + n0 + 5, &end, 10);
     // corrupt entry: ignore (valid: 1..64 sites per CTA, optionally with one of the hop
-    // kernels' flags 1 << 16 (occupancy-bounded build), 1 << 17 (tensor-core kernel) or
-    // 1 << 18 (paired-column kernel); a value no candidate list holds is ignored later too)
+    // kernels' flags 1 << 16 (occupancy-bounded build), 1 << 17 (tensor-core kernel),
+    // 1 << 18 (paired-column kernel) or 1 << 19 (bulk-staged kernel); a value no candidate
+    // list holds is ignored later too)
     const int ns_only = e.ns & 0xFFFF;
     const int flags = e.ns >> 16;
     if (end == line.c_str() + n0 + 5 || e.ns <= 0 || ns_only <= 0 || ns_only > 64 ||
-        (flags != 0 && flags != 1 && flags != 2 && flags != 4)) continue;
+        (flags != 0 && flags != 1 && flags != 2 && flags != 4 && flags != 8)) continue;
     e.ms = strtod(line.c_str() + m0 + 5, nullptr);
     c->tune[line.substr(q0 + 1, q1 - q0 - 1)] = e;
   }
@@ -312,11 +313,12 @@ bool capturing(cudaStream_t st) {
 }
 
 // tuner value flags of the hop kernels (sites per CTA in the low 16 bits): the
-// occupancy-bounded build of the CUDA-core kernel, the tcgen05 tensor-core kernel, and the
-// paired-column CUDA-core kernel
+// occupancy-bounded build of the CUDA-core kernel, the tcgen05 tensor-core kernel, the
+// paired-column CUDA-core kernel, and the bulk-staged CUDA-core kernel
 constexpr int kOccBit = 1 << 16;
 constexpr int kTcBit = 1 << 17;
 constexpr int kPairBit = 1 << 18;
+constexpr int kBulkBit = 1 << 19;
 
 // Pick sites-per-CTA for `key` by brute force over `cands`, timing each with events.
 // In-place outputs listed in `snaps` are saved before and restored after every trial run,
@@ -491,7 +493,8 @@ int hop_partitioned(mdwf_ctx* c, int prec, bool dag, bool r12, bool epi, const H
     q.x_begin = x0; q.x_end = x1;
     q.face_mode = mode; q.face = face; q.face_norm = face ? norm_of(face) : nullptr; q.face_base = base;
     cudaError_t err = tc ? launch_hop_tc(prec, dag, r12, epi, q, st)
-                         : launch_hop(prec, dag, r12, epi, (cfg & kOccBit) != 0, (cfg & kPairBit) != 0, false, q, st);
+                         : launch_hop(prec, dag, r12, epi, (cfg & kOccBit) != 0, (cfg & kPairBit) != 0, false,
+                                      (cfg & kBulkBit) != 0, q, st);
     c->launches++;
     if (err != cudaSuccess) { set_err("launch_hop", err); return MDWF_ERR_CUDA; }
     return MDWF_SUCCESS;
@@ -559,6 +562,15 @@ int hop(mdwf_ctx* c, int prec, bool dag, const Field& in, const Field& out, int 
         cands.push_back(ns | kPairBit);
       }
     }
+    // the bulk-staged kernel (undecomposed lattices: a partition's face timeslices take
+    // their t neighbours from the faces)
+    if (hop_bulk_supported(prec, q) && c->prm.t_ranks == 1) {
+      for (int ns : ns_candidates(W, MAXTHREADS, true)) {
+        q.ns = ns;
+        if (hop_smem_bytes(prec, q, e.on, false, true) > 200 * 1024) continue;
+        cands.push_back(ns | kBulkBit);
+      }
+    }
   }
   if (tc_ok) {
     for (int ns = 1; ns <= 16; ns *= 2) {
@@ -611,7 +623,8 @@ int hop(mdwf_ctx* c, int prec, bool dag, const Field& in, const Field& out, int 
       q.red.counter = c->counter;
     }
     cudaError_t err = tc ? launch_hop_tc(prec, dag, r12, e.on, q, st)
-                         : launch_hop(prec, dag, r12, e.on, (cfg & kOccBit) != 0, (cfg & kPairBit) != 0, emu, q, st);
+                         : launch_hop(prec, dag, r12, e.on, (cfg & kOccBit) != 0, (cfg & kPairBit) != 0, emu,
+                                      (cfg & kBulkBit) != 0, q, st);
     c->launches++;
     c->bytes += half_bytes(in, prec) + gauge_bytes(c, prec) + (q.has_center ? half_bytes(e.center, prec) : 0.0) +
                 (q.axpy_r ? 2.0 * half_bytes(e.raxpy, prec) : half_bytes(out, prec));

@@ -603,6 +603,182 @@ cudaError_t launch_hop2_prec(const HopParams& p, bool dag, bool r12, bool epi, i
   return epi ? launch_pair<P, false, false, true>(p, threads, smem, st) : launch_pair<P, false, false, false>(p, threads, smem, st);
 }
 
+// ---------------------------------------------------------------- bulk-staged hop
+// 16-bit storage: after phase 0 the CTA issues one asynchronous bulk copy (the TMA engine,
+// cp.async.bulk) per (site, direction) of the neighbour's whole row -- its 3 chunks
+// of every column, 48 W contiguous bytes -- into shared memory, all completing on one
+// mbarrier; the threads load their neighbours' scales meanwhile, wait once (bounded), and
+// run the hop loop from shared memory.  Same arithmetic as hop_kernel (bit-identical).
+
+constexpr int BULK_WAIT_SPINS = 1 << 24;   // bounded mbarrier wait (about a second)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool bulk_wait(uint32_t bar, uint32_t phase) {
+  for (int it = 0; it < BULK_WAIT_SPINS; it++) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    if (done) return true;
+    if (it >= 8) __nanosleep(64);
+  }
+  return false;
+}
+
+template <int P, bool DAG, bool R12, bool EPI>
+__global__ void __launch_bounds__(MAXTHREADS)
+hop_bulk_kernel(const __grid_constant__ HopParams p) {
+  static_assert(P == F16 || P == BF16 || P == I16, "bulk-staged hop: 16-bit storage only");
+  using C = float;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int Ls = p.in.Ls, nrhs = p.in.nrhs;
+  const int W = Ls * nrhs;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int site_l = tid / W;
+  const int col = tid - site_l * W;
+  const long long site0 = p.x_begin + (long long)blockIdx.x * p.ns;
+  const long long x_cb = site0 + site_l;
+  const bool active = x_cb < p.x_end;
+  const int nact = (int)min((long long)p.ns, p.x_end - site0);
+  constexpr int SF = DAG ? -1 : 1;
+  constexpr int LSTR = 20;
+  const BulkLayout BL = bulk_layout(p.ns, W);
+  C* slink = (C*)smem_raw;
+  unsigned* snbr = (unsigned*)(smem_raw + BL.nbr);
+  uint64_t* bar = (uint64_t*)(smem_raw + BL.bar);
+  unsigned char* rows = smem_raw + BL.rows;
+  unsigned char* epi_base = smem_raw + BL.epi;
+  const uint32_t rb = 48u * (uint32_t)W;   // bytes of one neighbour row
+
+  // one arrival (thread 0, with the transaction count of all the rows) completes the
+  // barrier's phase 0 once every row has landed
+  const uint32_t bar_a = smem_u32(bar);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_a) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar_a),
+                 "r"((uint32_t)nact * 8u * rb)
+                 : "memory");
+  }
+  for (int i = tid; i < p.ns * 8; i += nt) {
+    const long long x = site0 + (i >> 3);
+    if (x >= p.x_end) continue;
+    const int d = i & 7, mu = d & 3;
+    int c[4];
+    cb_coords(p.g, x, p.pout, c);
+    snbr[i] = (unsigned)nbr_cb(p.g, c, mu, d < 4 ? +1 : -1);
+    C U[18];
+    const bool flip = R12 && mu == 3 && p.t_bc < 0 &&
+                      (d < 4 ? c[3] == p.g.T - 1 && p.bc_hi : c[3] == 0 && p.bc_lo);
+    load_link<P, R12>(p.gauge, (x * 8 + d) * p.gs, U, flip);
+#pragma unroll
+    for (int k = 0; k < 18; k++) slink[i * LSTR + k] = U[k];
+  }
+  __syncthreads();
+
+  // the neighbour rows, one bulk copy each (every row of the CTA's active sites, whatever
+  // the thread count)
+  {
+    const unsigned char* src = (const unsigned char*)p.in.data;
+    for (int i = tid; i < nact * 8; i += nt)
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                       smem_u32(rows + (size_t)i * rb)),
+                   "l"(src + (size_t)snbr[i] * rb), "r"(rb), "r"(bar_a)
+                   : "memory");
+  }
+  // the scales of this thread's eight neighbour columns, while the rows arrive
+  const unsigned* nb = snbr + site_l * 8;
+  float nsc[8];
+#pragma unroll
+  for (int d = 0; d < 8; d++) nsc[d] = 1.0f;
+  if constexpr (P == F16 || P == I16) {
+    if (active) {
+#pragma unroll
+      for (int d = 0; d < 8; d++) nsc[d] = __ldg(p.in.norm + (long long)nb[d] * W + col);
+    }
+  }
+  if (!bulk_wait(bar_a, 0)) {
+    if (tid == 0 && p.status) atomicOr(p.status, 1);
+    bulk_wait(bar_a, 0);   // a second bounded wait before the rows' memory can be left
+  }
+
+  C acc[24];
+#pragma unroll
+  for (int i = 0; i < 24; i++) acc[i] = 0;
+  if (active) {
+    const C* lk = slink + site_l * 8 * LSTR;
+    const unsigned char* myrows = rows + (size_t)site_l * 8 * rb + (size_t)col * 16;
+    C h[12];
+#define HOPB_D(D, MU, SIG)                                                                \
+    { C nrm;                                                                              \
+      if (((D) == 7 && p.face_mode == 1) || ((D) == 3 && p.face_mode == 2)) {             \
+        nrm = load_face<P>(p, nb[D], col, h);                                             \
+      } else {                                                                            \
+        Raw16 r;                                                                          \
+        _Pragma("unroll") for (int c = 0; c < 3; c++)                                     \
+            r.q[c] = *(const uint4*)(myrows + (size_t)(D) * rb + (size_t)c * W * 16);      \
+        r.n = nsc[D];                                                                     \
+        nrm = proj16<P, MU, SIG>(r, h);                                                   \
+      }                                                                                   \
+      su3_recon<MU, SIG>(h, lk + (D) * LSTR, acc, nrm); }
+    HOPB_D(0, 0, SF) HOPB_D(4, 0, -SF) HOPB_D(1, 1, SF) HOPB_D(5, 1, -SF)
+    HOPB_D(2, 2, SF) HOPB_D(6, 2, -SF) HOPB_D(3, 3, SF) HOPB_D(7, 3, -SF)
+#undef HOPB_D
+  }
+
+  if constexpr (!EPI) {
+    if (active) store_site<P>(p.out, x_cb, col, acc);
+    return;
+  } else {
+    const int GS = tile_gstr(Ls);
+    const int ngrp = p.ns * nrhs;
+    C* tileH = (C*)epi_base;
+    const size_t toff = ((size_t)ngrp * GS * sizeof(C) + 15) & ~(size_t)15;
+    double* redsm = (double*)(epi_base + toff);
+    const int r = col / Ls, s = col - r * Ls;
+    const int grp = site_l * nrhs + r;
+    if (active) {
+      C* dst = tileH + grp * GS + s * TSTR;
+#pragma unroll
+      for (int k = 0; k < 24; k += 4) *(float4*)(dst + k) = make_float4(acc[k], acc[k + 1], acc[k + 2], acc[k + 3]);
+    }
+    __syncthreads();
+    hop_epilogue<P>(p, tileH, redsm, p.ns);
+  }
+}
+
+template <int P, bool DAG, bool R12, bool EPI>
+static cudaError_t launch_bulk(const HopParams& p, int threads, size_t smem, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(hop_bulk_kernel<P, DAG, R12, EPI>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const long long blocks = (p.x_end - p.x_begin + p.ns - 1) / p.ns;
+  HopParams q = p;
+  q.hcf = (float)p.hc; q.ccf = (float)p.cc; q.mff = (float)p.mf;
+  hop_bulk_kernel<P, DAG, R12, EPI><<<(unsigned)blocks, threads, smem, st>>>(q);
+  return cudaGetLastError();
+}
+
+// all (dagger, 12-real links, epilogue) variants of the bulk-staged kernel of one 16-bit
+// storage precision
+template <int P>
+cudaError_t launch_hop_bulk_prec(const HopParams& p, bool dag, bool r12, bool epi, int threads, size_t smem,
+                                 cudaStream_t st) {
+  if (dag) {
+    if (r12) return epi ? launch_bulk<P, true, true, true>(p, threads, smem, st) : launch_bulk<P, true, true, false>(p, threads, smem, st);
+    return epi ? launch_bulk<P, true, false, true>(p, threads, smem, st) : launch_bulk<P, true, false, false>(p, threads, smem, st);
+  }
+  if (r12) return epi ? launch_bulk<P, false, true, true>(p, threads, smem, st) : launch_bulk<P, false, true, false>(p, threads, smem, st);
+  return epi ? launch_bulk<P, false, false, true>(p, threads, smem, st) : launch_bulk<P, false, false, false>(p, threads, smem, st);
+}
+
 template <int P, bool DAG, bool R12, bool EPI, bool OCC = false, bool EMU = false>
 static cudaError_t launch_one(const HopParams& p, int threads, size_t smem, cudaStream_t st) {
   static bool attr_set = false;

@@ -46,12 +46,14 @@ struct HopParams {
 
 // pair: the paired-column kernel (32-bit compute types, nrhs * Ls even, ns * nrhs * Ls / 2
 // threads); occ: the occupancy-bounded build of a fused single-column 32-bit kernel; emu:
-// the emulated-FP64 (double-float) hop loop of the FP64 kernel
-size_t hop_smem_bytes(int prec, const HopParams& p, bool epi, bool pair = false);
+// the emulated-FP64 (double-float) hop loop of the FP64 kernel; bulk: the single-column
+// kernel with its neighbour rows staged in shared memory by bulk copies (16-bit storage)
+size_t hop_smem_bytes(int prec, const HopParams& p, bool epi, bool pair = false, bool bulk = false);
 int hop_threads(const HopParams& p, bool pair);
 bool hop_pair_supported(int prec, const HopParams& p);
-cudaError_t launch_hop(int prec, bool dag, bool r12, bool epi, bool occ, bool pair, bool emu, const HopParams& p,
-                       cudaStream_t st);
+bool hop_bulk_supported(int prec, const HopParams& p);
+cudaError_t launch_hop(int prec, bool dag, bool r12, bool epi, bool occ, bool pair, bool emu, bool bulk,
+                       const HopParams& p, cudaStream_t st);
 
 // one face of a T-partitioned lattice (partition.cu): for every site f of the local
 // timeslice starting at checkerboard index `first` (slice_vh sites) and every column, the

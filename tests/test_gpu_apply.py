@@ -147,14 +147,21 @@ PAIR_OPS = ["HOP_EO", "HOP_OE_DAG", "HOP_OE_M5INV", "MPC", "MPC_DAG", "MDAGM", "
             "MPC_SYM", "MPC_SYM_DAG"]
 
 
-@pytest.mark.parametrize("prec", ["f32", "f16", "bf16", "i16"])
+BULK_BIT = 1 << 19   # tuner value flag of the bulk-staged hop kernel
+
+
+@pytest.mark.parametrize("variant,prec", [("pair", "f32"), ("pair", "f16"), ("pair", "bf16"), ("pair", "i16"),
+                                          ("bulk", "f16"), ("bulk", "bf16"), ("bulk", "i16")])
 @pytest.mark.parametrize("ns", [1, 3, 16])
-def test_paired_hop_matches_oracle_and_single_column(prec, ns, monkeypatch):
-    """The paired-column hop kernel (two columns per thread on packed FP32 pairs) on every
-    hop-based op: parity with the oracle, and bit-identical to the single-column kernel
-    with the same sites per CTA (same roundings in the same order).  Cases: several tiles,
-    ragged last tiles (3 and 16 sites per CTA on 72- and 32-site half lattices), 1..12 RHS."""
+def test_variant_hop_matches_oracle_and_single_column(variant, prec, ns, monkeypatch):
+    """The paired-column hop kernel (two columns per thread on packed FP32 pairs) and the
+    bulk-staged one (neighbour rows copied into shared memory by bulk asynchronous copies)
+    on every hop-based op: parity with the oracle, and bit-identical to the single-column
+    kernel with the same sites per CTA (same roundings in the same order).  Cases: several
+    tiles, ragged last tiles (3 and 16 sites per CTA on 72- and 32-site half lattices),
+    1..12 RHS."""
     monkeypatch.setenv("MDWF_TC", "0")
+    flag = PAIR_BIT if variant == "pair" else BULK_BIT
     for dims, Ls, nrhs in PAIR_CASES:
         if ns * nrhs * Ls > 256:
             continue      # more threads than a CTA of the single-column kernel takes
@@ -163,7 +170,7 @@ def test_paired_hop_matches_oracle_and_single_column(prec, ns, monkeypatch):
         for op in PAIR_OPS:
             monkeypatch.setenv("MDWF_FORCE_NS", str(ns))
             single = _gpu_apply(m, ctx, op, prec, psi, nrhs)
-            monkeypatch.setenv("MDWF_FORCE_NS", str(PAIR_BIT | ns))
+            monkeypatch.setenv("MDWF_FORCE_NS", str(flag | ns))
             got = _gpu_apply(m, ctx, op, prec, psi, nrhs)
             ref = np.stack([_oracle(op, Ub, psi[r], p, par) for r in range(nrhs)])
             keep = _mask(op, par, ref.shape)
