@@ -7,6 +7,7 @@
 // Thread layout as in the hop kernels: a CTA owns ns 4D sites, thread (site_l, r, s).
 #include "mdwf_impl.cuh"
 #include "mdwf_kernels.h"
+#include "mdwf_epi.cuh"
 
 namespace mdwf {
 
@@ -84,6 +85,9 @@ __global__ void __launch_bounds__(MAXTHREADS) axpby_kernel(const __grid_constant
 }
 
 // CG step: x += alpha p ; p = r + beta p ; phat = chain(p).   a = p, b = r, c = phat.
+// A chain of one bidiagonal op (the left form's phat = D5 p) is applied per site from the
+// new p of the slices s +- 1 (one 16-byte-row tile, one barrier); other chains run as
+// column passes over the tile.
 template <int PX, int P>
 __global__ void __launch_bounds__(MAXTHREADS) cg_update_kernel(const __grid_constant__ SLParams p) {
   using C = typename PT<P>::C;
@@ -95,6 +99,58 @@ __global__ void __launch_bounds__(MAXTHREADS) cg_update_kernel(const __grid_cons
   const bool active = x_cb < p.vh;
   const int r = col / Ls, s = col - r * Ls, grp = site_l * nrhs + r;
   C* tile = (C*)smem_raw;
+  if constexpr (sizeof(C) == 4) {
+    const SOp& o = p.chain.op[0];
+    if (p.c.data != nullptr && o.kind == SOP_BIDIAG && p.chain.op[1].kind == SOP_NONE) {
+      // tile rows [grp][s][TSTR]: the new p of every 5D site of the CTA
+      C pv[24];
+      if (active) {
+        const double alpha = p.red.cg[r].alpha;
+        C rv[24];
+        load_site<P>(p.a, x_cb, col, pv);
+        if (pick<CX>(p.red.cg[r].alpha_f, alpha) != (CX)0) {
+          CX xv[24];
+          load_site<PX>(p.x, x_cb, col, xv);
+          const CX ax = pick<CX>(p.red.cg[r].alpha_f, alpha);
+#pragma unroll
+          for (int k = 0; k < 24; k++) xv[k] += ax * (CX)pv[k];
+          store_site<PX>(p.x, x_cb, col, xv);
+        }
+        load_site<P>(p.b, x_cb, col, rv);
+        const C bt = pick<C>(p.red.cg[r].beta_f, p.red.cg[r].beta);
+#pragma unroll
+        for (int k = 0; k < 24; k++) pv[k] = rv[k] + bt * pv[k];
+        store_site<P>(p.a, x_cb, col, pv);
+        C* row = tile + (grp * Ls + s) * TSTR;
+#pragma unroll
+        for (int k = 0; k < 24; k += 4) *(float4*)(row + k) = make_float4(pv[k], pv[k + 1], pv[k + 2], pv[k + 3]);
+      }
+      __syncthreads();
+      if (active) {
+        // upper spins (0, 1) of each colour from slice su, lower ones (2, 3) from sl
+        const SNbr<C> n = s_nbr<C>(o, s, Ls, pick<C>(p.mff, p.mf));
+        const C a = sop_a<C>(o);
+        const C* ru = tile + (grp * Ls + n.su) * TSTR;
+        const C* rl = tile + (grp * Ls + n.sl) * TSTR;
+        C v[24];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          const float4 u = *(const float4*)(ru + 8 * c);
+          const float4 l = *(const float4*)(rl + 8 * c + 4);
+          v[8 * c + 0] = a * pv[8 * c + 0] + n.fu * u.x;
+          v[8 * c + 1] = a * pv[8 * c + 1] + n.fu * u.y;
+          v[8 * c + 2] = a * pv[8 * c + 2] + n.fu * u.z;
+          v[8 * c + 3] = a * pv[8 * c + 3] + n.fu * u.w;
+          v[8 * c + 4] = a * pv[8 * c + 4] + n.fl * l.x;
+          v[8 * c + 5] = a * pv[8 * c + 5] + n.fl * l.y;
+          v[8 * c + 6] = a * pv[8 * c + 6] + n.fl * l.z;
+          v[8 * c + 7] = a * pv[8 * c + 7] + n.fl * l.w;
+        }
+        store_site<P>(p.c, x_cb, col, v);
+      }
+      return;
+    }
+  }
   if (active) {
     const double alpha = p.red.cg[r].alpha;
     C pv[24], rv[24];
@@ -211,7 +267,10 @@ static cudaError_t go(K kern, const SLParams& p, int W, size_t smem, cudaStream_
 }
 
 static size_t tile_bytes(int prec, const Field& f, int ns) {
-  return (size_t)ns * f.nrhs * 24 * (f.Ls + 1) * (prec == F64 ? 8 : 4);
+  // column tile [grp][24][Ls + 1], or (cg_update, one bidiagonal op) 16-byte rows [grp][s][TSTR]
+  const size_t col = (size_t)ns * f.nrhs * 24 * (f.Ls + 1) * (prec == F64 ? 8 : 4);
+  const size_t rows = (size_t)ns * f.nrhs * f.Ls * TSTR * 4;
+  return col > rows ? col : rows;
 }
 
 cudaError_t launch_chain(int prec, const SLParams& p, cudaStream_t st) {
