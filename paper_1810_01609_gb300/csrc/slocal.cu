@@ -106,20 +106,17 @@ __global__ void __launch_bounds__(MAXTHREADS) cg_update_kernel(const __grid_cons
       C pv[24];
       if (active) {
         const double alpha = p.red.cg[r].alpha;
-        const CX ax = pick<CX>(p.red.cg[r].alpha_f, alpha);
-        const bool upd = ax != (CX)0;
-        // every load before the first store: x, p and r may alias as far as the compiler
-        // knows, so a load after a store would wait for it
         C rv[24];
-        CX xv[24];
         load_site<P>(p.a, x_cb, col, pv);
-        load_site<P>(p.b, x_cb, col, rv);
-        if (upd) load_site<PX>(p.x, x_cb, col, xv);
-        if (upd) {
+        if (pick<CX>(p.red.cg[r].alpha_f, alpha) != (CX)0) {
+          CX xv[24];
+          load_site<PX>(p.x, x_cb, col, xv);
+          const CX ax = pick<CX>(p.red.cg[r].alpha_f, alpha);
 #pragma unroll
           for (int k = 0; k < 24; k++) xv[k] += ax * (CX)pv[k];
           store_site<PX>(p.x, x_cb, col, xv);
         }
+        load_site<P>(p.b, x_cb, col, rv);
         const C bt = pick<C>(p.red.cg[r].beta_f, p.red.cg[r].beta);
 #pragma unroll
         for (int k = 0; k < 24; k++) pv[k] = rv[k] + bt * pv[k];
