@@ -776,17 +776,17 @@ int apply_mpc(mdwf_ctx* c, int prec, const Field& in, const Field& out, cudaStre
   return hop(c, prec, false, w, out, 1, e2, red_none(), st);
 }
 
-// M_pc^+ in = in - D5^+ A5^-+ H_eo^+ (A5^-+ D5^+ H_oe^+ in) / 4: both A5^-+ after their hops
-// (the hops commute with the s-direction operators), so in is read as it is
 int apply_mpc_dag(mdwf_ctx* c, int prec, const Field& in, const Field& out, cudaStream_t st) {
   const Ops o = ops_of(c, c->prm.mf);
-  Field y;
+  Field qt, y;
+  CKS(ws_half(c, "mpcd_q", prec, in.nrhs, &qt));
   CKS(ws_half(c, "mpcd_y", prec, in.nrhs, &y));
+  CKS(sl_chain(c, prec, qt, in, chain(o.A5inv(true)), 1.0, nullptr, 0.0, o.mf, st));
   Epi e3;
   e3.on = true; e3.post = chain(o.D5(true), o.A5inv(true)); e3.mf = o.mf;
-  CKS(hop(c, prec, true, in, y, 0, e3, red_none(), st));
+  CKS(hop(c, prec, true, qt, y, 0, e3, red_none(), st));
   Epi e4;
-  e4.on = true; e4.post = chain(o.A5inv(true), o.D5(true)); e4.hc = -0.25; e4.center = in;
+  e4.on = true; e4.post = chain(o.D5(true)); e4.hc = -0.25; e4.center = qt; e4.cop = chain(o.A5(true));
   e4.mf = o.mf;
   return hop(c, prec, true, y, out, 1, e4, red_none(), st);
 }
@@ -902,19 +902,15 @@ int cg_iteration(mdwf_ctx* c, const CGSet& v, cudaStream_t st) {
   Epi e1;  // w_e = D5 A5^-1 H_eo phat
   e1.on = true; e1.post = chain(o.A5inv(false), o.D5(false)); e1.mf = o.mf;
   CKS(hop(c, P, false, v.ph, v.w, 0, e1, red_none(), st));
-  // M^+ q = q - D5^+ H_eo^+ A5^-+ D5^+ H_oe^+ A5^-+ q / 4.  The hops act on the 4D index
-  // and the s-direction operators on s only, so they commute: the leading A5^-+ moves
-  // past H_oe^+ into the last kernel's post chain, and K2 stores q itself (no final
-  // column pass) which K4 then takes as its centre with no s-operator.
-  Epi e2;  // q = p - A5^-1 H_oe w / 4 ; |q|^2 -> alpha ; store q
+  Epi e2;  // q = p - A5^-1 H_oe w / 4 ; |q|^2 -> alpha ; store qt = A5^-+ q
   e2.on = true; e2.post = chain(o.A5inv(false)); e2.hc = -0.25; e2.center = v.p; e2.norm_pre = true;
-  e2.mf = o.mf;
+  e2.fin = chain(o.A5inv(true)); e2.mf = o.mf;
   CKS(hop(c, P, false, v.w, v.qt, 1, e2, red_cg(c, RED_CG_ALPHA, v.nrhs), st));
-  Epi e3;  // y_e = A5^-+ D5^+ H_oe^+ q
+  Epi e3;  // y_e = A5^-+ D5^+ H_oe^+ qt
   e3.on = true; e3.post = chain(o.D5(true), o.A5inv(true)); e3.mf = o.mf;
   CKS(hop(c, P, true, v.qt, v.y, 0, e3, red_none(), st));
-  Epi e4;  // s = q - D5^+ A5^-+ H_eo^+ y / 4 ; r -= alpha s ; |r|^2 -> beta
-  e4.on = true; e4.post = chain(o.A5inv(true), o.D5(true)); e4.hc = -0.25; e4.center = v.qt;
+  Epi e4;  // s = A5^+ qt - D5^+ H_eo^+ y / 4 ; r -= alpha s ; |r|^2 -> beta
+  e4.on = true; e4.post = chain(o.D5(true)); e4.hc = -0.25; e4.center = v.qt; e4.cop = chain(o.A5(true));
   e4.raxpy = v.r; e4.mf = o.mf;
   CKS(hop(c, P, true, v.y, v.r, 1, e4, red_cg(c, RED_CG_BETA, v.nrhs), st));
   return cg_update(c, v, chain(o.D5(false)), true, st);
