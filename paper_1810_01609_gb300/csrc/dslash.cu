@@ -40,8 +40,9 @@ size_t hop_smem_bytes(int prec, const HopParams& p, bool epi, bool pair, bool bu
     const size_t pre = (size_t)bulk_layout(p.ns, p.in.nrhs * p.in.Ls).epi;
     return epi ? pre + epi_smem_bytes(csz, p.ns, p.in.nrhs, p.in.Ls, p.has_center, hop_threads(p, false)) : pre;
   }
-  // staged links: 18 float2 per link for the paired kernel, else 18 (F64) or 20 reals
-  const size_t links = pair ? (size_t)p.ns * 8 * 18 * 8 : (size_t)p.ns * 8 * (prec == F64 ? 18 : 20) * csz;
+  // staged links: 18 float2 per link for the paired kernel, else 18 (F64) or 20 reals;
+  // 16 bytes per site of bank offset
+  const size_t links = pair ? (size_t)p.ns * (8 * 18 + 2) * 8 : (size_t)p.ns * (8 * (prec == F64 ? 18 : 20) * csz + 16);
   const size_t nbr = (size_t)((p.ns * 8 + 3) & ~3) * 4;
   const size_t pre = (links + nbr + 15) & ~(size_t)15;
   if (!epi) return pre;

@@ -369,6 +369,9 @@ __device__ __forceinline__ void su3_recon_emu(const dfl h[12], const dfl* U, dac
 
 // Link staging stride in shared memory (compute-precision reals per link, 16-byte rows)
 template <typename C> __host__ __device__ constexpr int link_stride() { return sizeof(C) == 8 ? 18 : 20; }
+// ... and per site: its 8 links plus 16 bytes, so that the sites sharing a warp (whose
+// threads read their own site's link) start 4 banks apart instead of on the same bank
+template <typename C> __host__ __device__ constexpr int site_link_stride() { return 8 * link_stride<C>() + 16 / (int)sizeof(C); }
 
 // OCC: the occupancy-bounded build (at least 4 CTAs of MAXTHREADS per SM, i.e. at most 64
 // registers, a few spilled); the autotuner picks it or the unbounded one per kernel and
@@ -391,9 +394,10 @@ hop_kernel(const __grid_constant__ HopParams p) {
   const bool active = x_cb < p.x_end;
   constexpr int SF = DAG ? -1 : 1;
   constexpr int LSTR = link_stride<C>();
+  constexpr int SSTR = site_link_stride<C>();
   // shared: links of the CTA's sites (compute precision), neighbour table, epilogue
   C* slink = (C*)smem_raw;
-  unsigned* snbr = (unsigned*)(slink + p.ns * 8 * LSTR);
+  unsigned* snbr = (unsigned*)(slink + p.ns * SSTR);
   unsigned char* epi_base = (unsigned char*)(snbr + ((p.ns * 8 + 3) & ~3));
 
   // phase 0: one thread per (site, direction) loads and converts the link, and finds the
@@ -410,12 +414,12 @@ hop_kernel(const __grid_constant__ HopParams p) {
                       (d < 4 ? c[3] == p.g.T - 1 && p.bc_hi : c[3] == 0 && p.bc_lo);
     load_link<P, R12>(p.gauge, (x * 8 + d) * p.gs, U, flip);
     if constexpr (EMU) {
-      dfl* dl = (dfl*)(slink + i * LSTR);   // 18 pairs in the 18 doubles' space
+      dfl* dl = (dfl*)(slink + (i >> 3) * SSTR + (i & 7) * LSTR);   // 18 pairs in the 18 doubles' space
 #pragma unroll
       for (int k = 0; k < 18; k++) dl[k] = split_f64(U[k]);
     } else {
 #pragma unroll
-      for (int k = 0; k < 18; k++) slink[i * LSTR + k] = U[k];
+      for (int k = 0; k < 18; k++) slink[(i >> 3) * SSTR + (i & 7) * LSTR + k] = U[k];
     }
   }
   __syncthreads();
@@ -426,7 +430,7 @@ hop_kernel(const __grid_constant__ HopParams p) {
   if constexpr (EMU) {
     if (active) {
       const unsigned* nb = snbr + site_l * 8;
-      const dfl* lk = (const dfl*)(slink + site_l * 8 * LSTR);
+      const dfl* lk = (const dfl*)(slink + site_l * SSTR);
       dacc da[24];
 #pragma unroll
       for (int i = 0; i < 24; i++) da[i] = {0.0f, 0.0f};
@@ -443,7 +447,7 @@ hop_kernel(const __grid_constant__ HopParams p) {
     }
   } else if (active) {
     const unsigned* nb = snbr + site_l * 8;
-    const C* lk = slink + site_l * 8 * LSTR;
+    const C* lk = slink + site_l * SSTR;
     C h[12];
 #define HOP_D(D, MU, SIG)                                                                 \
     { const C nrm = ((D) == 7 && p.face_mode == 1) || ((D) == 3 && p.face_mode == 2)       \
@@ -502,8 +506,9 @@ hop2_kernel(const __grid_constant__ HopParams p) {
   constexpr int SF = DAG ? -1 : 1;
   // shared: links as duplicated pairs (18 float2 = 144 bytes per link), neighbour table,
   // epilogue
+  constexpr int SSTR2 = 8 * 18 + 2;   // float2 per site: 8 links + 16 bytes (bank offset)
   float2* slink = (float2*)smem_raw;
-  unsigned* snbr = (unsigned*)(slink + p.ns * 8 * 18);
+  unsigned* snbr = (unsigned*)(slink + p.ns * SSTR2);
   unsigned char* epi_base = (unsigned char*)(snbr + ((p.ns * 8 + 3) & ~3));
 
   for (int i = tid; i < p.ns * 8; i += nt) {
@@ -517,7 +522,7 @@ hop2_kernel(const __grid_constant__ HopParams p) {
     const bool flip = R12 && mu == 3 && p.t_bc < 0 &&
                       (d < 4 ? c[3] == p.g.T - 1 && p.bc_hi : c[3] == 0 && p.bc_lo);
     load_link<P, R12>(p.gauge, (x * 8 + d) * p.gs, U, flip);
-    float4* dst = (float4*)(slink + i * 18);
+    float4* dst = (float4*)(slink + (i >> 3) * SSTR2 + (i & 7) * 18);
 #pragma unroll
     for (int k = 0; k < 18; k += 2) dst[k >> 1] = make_float4(U[k], U[k], U[k + 1], U[k + 1]);
   }
@@ -528,7 +533,7 @@ hop2_kernel(const __grid_constant__ HopParams p) {
   for (int i = 0; i < 24; i++) acc[i] = make_float2(0.0f, 0.0f);
   if (active) {
     const unsigned* nb = snbr + site_l * 8;
-    const float2* lk = slink + site_l * 8 * 18;
+    const float2* lk = slink + site_l * SSTR2;
     C hA[12], hB[12];
     float2 h[12];
 #define HOP2_D(D, MU, SIG)                                                                \
@@ -645,6 +650,7 @@ hop_bulk_kernel(const __grid_constant__ HopParams p) {
   const int nact = (int)min((long long)p.ns, p.x_end - site0);
   constexpr int SF = DAG ? -1 : 1;
   constexpr int LSTR = 20;
+  constexpr int SSTR = site_link_stride<C>();
   const BulkLayout BL = bulk_layout(p.ns, W);
   C* slink = (C*)smem_raw;
   unsigned* snbr = (unsigned*)(smem_raw + BL.nbr);
@@ -675,7 +681,7 @@ hop_bulk_kernel(const __grid_constant__ HopParams p) {
                       (d < 4 ? c[3] == p.g.T - 1 && p.bc_hi : c[3] == 0 && p.bc_lo);
     load_link<P, R12>(p.gauge, (x * 8 + d) * p.gs, U, flip);
 #pragma unroll
-    for (int k = 0; k < 18; k++) slink[i * LSTR + k] = U[k];
+    for (int k = 0; k < 18; k++) slink[(i >> 3) * SSTR + (i & 7) * LSTR + k] = U[k];
   }
   __syncthreads();
 
@@ -709,7 +715,7 @@ hop_bulk_kernel(const __grid_constant__ HopParams p) {
 #pragma unroll
   for (int i = 0; i < 24; i++) acc[i] = 0;
   if (active) {
-    const C* lk = slink + site_l * 8 * LSTR;
+    const C* lk = slink + site_l * SSTR;
     const unsigned char* myrows = rows + (size_t)site_l * 8 * rb + (size_t)col * 16;
     C h[12];
 #define HOPB_D(D, MU, SIG)                                                                \

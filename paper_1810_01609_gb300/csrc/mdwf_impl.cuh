@@ -384,12 +384,13 @@ __host__ __device__ inline int tile_gstr(int Ls) {
   return base + ((24 - (base & 31)) & 31);
 }
 
-// Shared-memory layout of the bulk-staged hop kernel: links (20 floats each), neighbour
-// table, mbarrier, the neighbour rows (48 W bytes each, 128-byte aligned), epilogue.
+// Shared-memory layout of the bulk-staged hop kernel: links (20 floats each, 8 per site
+// plus 4 floats of bank offset), neighbour table, mbarrier, the neighbour rows (48 W bytes
+// each, 128-byte aligned), epilogue.
 struct BulkLayout { int nbr, bar, rows, epi; };
 __host__ __device__ inline BulkLayout bulk_layout(int ns, int W) {
   BulkLayout L;
-  L.nbr = ns * 8 * 20 * 4;
+  L.nbr = ns * (8 * 20 + 4) * 4;
   L.bar = (L.nbr + ((ns * 8 + 3) & ~3) * 4 + 15) & ~15;
   L.rows = (L.bar + 16 + 127) & ~127;
   L.epi = L.rows + ns * 8 * 48 * W;
