@@ -49,8 +49,16 @@ def test_host_side_argument_validation():
             raise AssertionError("accepted %r" % bad)
         except m.MdwfError as e:
             assert e.code == m.MDWF_ERR_ARG
+    assert m.mdwf_default_params().f64_emulation == 1
     ctx = m.mdwf_create(m.mdwf_default_params())
     assert m.mdwf_field_bytes(ctx, 2, 1) > m.mdwf_field_bytes(ctx, 3, 1)
+    # emulated FP64 uses the FP64 storage layout
+    assert m.mdwf_field_bytes(ctx, m.PRECS["f64e"], 1) == m.mdwf_field_bytes(ctx, 0, 1)
+    # the one-call propagator rejects missing buffers before touching the device
+    infos = (m.mdwf_solve_info * 1)()
+    sp = m.mdwf_default_solve_params()
+    code = m.load().mdwf_propagator(ctx, 1, None, None, m.MDWF_HOST, ctypes.byref(sp), infos, None)
+    assert code == m.MDWF_ERR_ARG
     try:
         m.mdwf_field_bytes(ctx, 7, 1)
         raise AssertionError
