@@ -367,19 +367,6 @@ __device__ __forceinline__ void su3_recon_emu(const dfl h[12], const dfl* U, dac
   }
 }
 
-// Ask L2 for the 16-byte chunks (and the scale) of one site column of a field: the fused
-// epilogue reads its centre and its r only after the hop and a barrier, so their DRAM
-// latency would otherwise be exposed; the prefetch needs no registers.
-template <int P>
-__device__ __forceinline__ void prefetch_site(const Field& f, long long x_cb, int col) {
-  constexpr int NC = PT<P>::NC;
-  const long long W = f.W();
-  const uint4* d = (const uint4*)f.data + (x_cb * NC) * W + col;
-#pragma unroll
-  for (int c = 0; c < NC; c++) asm volatile("prefetch.global.L2 [%0];" ::"l"(d + c * W));
-  if constexpr (PT<P>::NORM) asm volatile("prefetch.global.L2 [%0];" ::"l"(f.norm + x_cb * W + col));
-}
-
 // Link staging stride in shared memory (compute-precision reals per link, 16-byte rows)
 template <typename C> __host__ __device__ constexpr int link_stride() { return sizeof(C) == 8 ? 18 : 20; }
 // ... and per site: its 8 links plus 16 bytes, so that the sites sharing a warp (whose
@@ -413,12 +400,6 @@ hop_kernel(const __grid_constant__ HopParams p) {
   unsigned* snbr = (unsigned*)(slink + p.ns * SSTR);
   unsigned char* epi_base = (unsigned char*)(snbr + ((p.ns * 8 + 3) & ~3));
 
-  if constexpr (EPI) {
-    if (active) {
-      if (p.has_center) prefetch_site<P>(p.center, x_cb, col);
-      if (p.axpy_r) prefetch_site<P>(p.raxpy, x_cb, col);
-    }
-  }
   // phase 0: one thread per (site, direction) loads and converts the link, and finds the
   // neighbour; forward links carry the boundary phase on t at T-1, backward ones on t at 0
   for (int i = tid; i < p.ns * 8; i += nt) {
